@@ -1,0 +1,383 @@
+/*
+ * Precision-generic body of the CPU oracle for the batched 2x2 SVD of
+ * V. Novakovic, "Batched computation of the singular value decompositions of
+ * order two by the AVX-512 vectorization" (arXiv 2005.07403).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is included by svd2_oracle.c once per
+ * floating type; it is plain, slow, scalar C that follows the paper's steps in
+ * the paper's order and notation, one matrix at a time.  It shares nothing with
+ * the CUDA path.  Only tests, the smoke check and the bench's CPU baseline use it.
+ *
+ * Before inclusion the includer defines:
+ *   T            the floating type
+ *   SFX(name)    name mangling for this type (e.g. name##_d)
+ *   T_MAX        largest finite T           (DBL_MAX in the paper)
+ *   T_TRUE_MIN   smallest positive T        (DBL_TRUE_MIN in the paper, Eq. 1)
+ *   T_MAX_EXP    T's MAX_EXP                (h = T_MAX_EXP - 3, Sec. 2.1)
+ *   T_SQRT_MAX   RN(sqrt(T_MAX))            (bound in Eq. 14)
+ *   T_FMA, T_SQRT, T_FMIN, T_FMAX, T_FABS, T_COPYSIGN, T_LOGB, T_SCALBN
+ *
+ * Readings of the paper taken here (each also listed in the design notes):
+ *  - hypot is the paper's own naive formula (Sec. 5, text before Fig. 4), so the
+ *    result is a fixed sequence of correctly rounded operations;
+ *  - invsqrt(x) = 1/sqrt(x) with IEEE sqrt and IEEE division (Sec. 6, the first
+ *    remedy named before Fig. 8);
+ *  - fmin/fmax are C's; every use below has a non-NaN constant second operand
+ *    and no (+0,-0) pair can reach them, so C's semantics coincide with the
+ *    relaxed ones of Sec. 2 (second argument returned for a NaN first);
+ *  - exp2 of Sec. 2.1 is logb (floor(lg|a|), exact for subnormals, -inf for 0);
+ *    SCALEF is scalbn (round to nearest for subnormal results);
+ *  - s stays a T as in Eq. 2, with T_MAX for the all-zero matrix;
+ *  - the d's of the real case are +-1 carrying the sign bit (Eq. 10; Fig. 7
+ *    applies them by XOR, which is the same as multiplying by +-1);
+ *  - the U expansion after Eq. 29 is used as printed: inner complex value, then
+ *    the complex product with d_ii (Eq. 5), then the real factor c; the V of
+ *    Eq. 29 is formed as v11 = cos(psi), v12 = cos(psi) tan(psi),
+ *    v21 = -d~22 (cos(psi) tan(psi)), v22 = d~22 cos(psi).
+ */
+
+/* ---- Sec. 2 and Sec. 5 (before Fig. 4): hypot(a,b) without exponent
+ * adjustment.  a' = max(|a|,|b|), b' = min(|a|,|b|), a+ = max(a', TRUE_MIN),
+ * q+ = b'/a+ <= 1, c = a' * sqrt(fma(q+, q+, 1)).  hypot(a,b) = 0 iff a = b = 0. */
+static inline T SFX(hypot_naive)(T a, T b)
+{
+    T aa = T_FABS(a), ab = T_FABS(b);
+    T ap = T_FMAX(aa, ab);
+    T bp = T_FMIN(aa, ab);
+    T apl = T_FMAX(ap, T_TRUE_MIN);
+    T q = bp / apl;
+    return ap * T_SQRT(T_FMA(q, q, (T)1));
+}
+
+/* Sec. 2 (cosine formulas of Eq. 7, 15, 16) with the remedy of Sec. 6:
+ * invsqrt(x) = 1/sqrt(x). */
+static inline T SFX(invsqrt)(T x)
+{
+    return (T)1 / T_SQRT(x);
+}
+
+/* Eq. 1 as vectorized in Fig. 7 and Fig. 9: e^{i arg z} for z = (re, im) with
+ * |z| = az given.  cos(arg z) = fmin(|Re z| / |z|, 1) with the sign of Re z
+ * (the 0/0 NaN of z = 0 becomes 1 through fmin); sin(arg z) =
+ * Im z / max(|z|, TRUE_MIN). */
+static inline void SFX(cis_arg)(T re, T im, T az, T *cr, T *ci)
+{
+    *cr = T_COPYSIGN(T_FMIN(T_FABS(re) / az, (T)1), re);
+    *ci = im / T_FMAX(az, T_TRUE_MIN);
+}
+
+/* Sec. 2.1, Eq. 2 and Fig. 3: s = min{T_MAX, min_ij (h - exp2 part_ij)} over the
+ * np parts (4 real, 8 complex), h = MAX_EXP - 3, exp2 0 = -inf. */
+static inline T SFX(scale_exponent)(const T *part, int np)
+{
+    const T h = (T)(T_MAX_EXP - 3);
+    T s = T_MAX;
+    for (int k = 0; k < np; ++k)
+        s = T_FMIN(s, h - T_LOGB(part[k]));
+    return s;
+}
+
+/* Fig. 3, last line: a_hat = SCALEF(a, s) = a * 2^s.  With s = T_MAX (all parts
+ * zero) the parts are zeros and are kept as they are (0 * 2^s = 0, Sec. 2.1). */
+static inline T SFX(scalef)(T a, T s)
+{
+    if (s == T_MAX)
+        return a;
+    return T_SCALBN(a, (int)s);
+}
+
+/*
+ * One real 2x2 SVD, Sec. 2 with the real-case simplifications of Eq. 10 and the
+ * figures' R-comments.  A[i][j] = a_{i+1,j+1}.  Outputs: U, V (row-major 2x2),
+ * the scaled singular values sigma'_max >= sigma'_min (Eq. 17), the scale
+ * exponent s (Eq. 2) and the two pivot bits (bit 0: P_c swapped the columns,
+ * bit 1: P_r* swapped the rows).
+ */
+static inline void SFX(svd2_real)(const T A[2][2], T U[2][2], T V[2][2],
+                           T *smax, T *smin, T *s_out, int *piv)
+{
+    /* Phase 1, Sec. 2.1: scale A by 2^s (Eq. 2, Fig. 3). */
+    const T parts[4] = { A[0][0], A[1][0], A[0][1], A[1][1] };
+    const T s = SFX(scale_exponent)(parts, 4);
+    T Ah[2][2], absAh[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            Ah[i][j] = SFX(scalef)(A[i][j], s);
+            absAh[i][j] = T_FABS(Ah[i][j]);        /* Fig. 4, real case */
+        }
+
+    /* Phase 2, Sec. 2.2.  Column norms, Eq. 3 / Fig. 4. */
+    T nrm[2];
+    for (int j = 0; j < 2; ++j)
+        nrm[j] = SFX(hypot_naive)(absAh[0][j], absAh[1][j]);
+
+    /* Column pivoting P_c (Fig. 5): swap iff ||a_1|| < ||a_2||. */
+    const int pc = nrm[0] < nrm[1];
+    T A1[2][2], absA1[2][2], nrm1[2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            A1[i][j] = Ah[i][pc ? 1 - j : j];
+            absA1[i][j] = absAh[i][pc ? 1 - j : j];
+        }
+    nrm1[0] = nrm[pc ? 1 : 0];
+    nrm1[1] = nrm[pc ? 0 : 1];
+
+    /* Row sorting P_r* (Fig. 6): swap iff |a'_11| < |a'_21|. */
+    const int pr = absA1[0][0] < absA1[1][0];
+    T A2[2][2], absA2[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            A2[i][j] = A1[pr ? 1 - i : i][j];
+            absA2[i][j] = absA1[pr ? 1 - i : i][j];
+        }
+
+    /* D* of Eq. 10 (Fig. 7, real case): d_ii = sign a''_i1, a'''_i1 = |a''_i1|,
+     * a'''_i2 = d_ii a''_i2. */
+    T d[2], A3[2][2];
+    for (int i = 0; i < 2; ++i) {
+        d[i] = T_COPYSIGN((T)1, A2[i][0]);
+        A3[i][0] = absA2[i][0];
+        A3[i][1] = d[i] * A2[i][1];
+    }
+
+    /* QR by the Givens rotation Q_alpha*, Eq. 6 and Eq. 7 (Fig. 8).  r11 is the
+     * already known norm of the first column. */
+    const T r11 = nrm1[0];
+    const T mtana = T_FMAX(A3[1][0] / A3[0][0], (T)0);      /* -tan(alpha) */
+    const T tana = -mtana;
+    const T cosa = SFX(invsqrt)(T_FMA(tana, tana, (T)1));
+    const T r12p = cosa * T_FMA(mtana, A3[1][1], A3[0][1]);  /* r'_12 */
+    const T r22pp = cosa * T_FMA(tana, A3[0][1], A3[1][1]);  /* r''_22: -(-tan a * a12) + a22 */
+
+    /* D~ of Eq. 8 and D^* of Eq. 9, real case (Eq. 10, Fig. 9). */
+    const T dt = T_COPYSIGN((T)1, r12p);     /* d~_22 */
+    const T r12 = T_FABS(r12p);
+    const T r22p = r22pp * dt;               /* r'_22 = r''_22 d~_22 */
+    const T dh = T_COPYSIGN((T)1, r22p);     /* d^_22 */
+    const T r22 = T_FABS(r22p);
+
+    /* Phase 3, Sec. 2.3: SVD of R, Eq. 13 - Eq. 17 (Fig. 10). */
+    const T x = T_FMAX(r12 / r11, (T)0);
+    const T y = T_FMAX(r22 / r11, (T)0);
+    const T num = ((T)2 * T_FMIN(x, y)) * T_FMAX(x, y);
+    const T den = T_FMA(x - y, x + y, (T)1);
+    const T tan2p = -T_FMIN(T_FMAX(num / den, (T)0), T_SQRT_MAX);   /* Eq. 14 */
+    const T tanp = tan2p / ((T)1 + T_SQRT(T_FMA(tan2p, tan2p, (T)1))); /* Eq. 15 */
+    const T sec2p = T_FMA(tanp, tanp, (T)1);
+    const T cosp = SFX(invsqrt)(sec2p);
+    const T tanq = T_FMA(y, tanp, -x);                               /* Eq. 16 */
+    const T sec2q = T_FMA(tanq, tanq, (T)1);
+    const T cosq = SFX(invsqrt)(sec2q);
+    const T cpq = cosp * cosq;
+    *smax = (cpq * sec2q) * r11;                                     /* Eq. 17 */
+    *smin = (cpq * sec2p) * r22;
+
+    /* Phase 4: Eq. 29 with c = cos(alpha) cos(phi), t = -tan(alpha) tan(phi).
+     * Real case: d11, d22, d^22 are +-1, so the complex products reduce to
+     * sign changes. */
+    const T c = cosa * cosp;
+    const T t = -(tana * tanp);
+    T Ur[2][2];                              /* P_r* U */
+    Ur[0][0] = c * (d[0] * T_FMA(dh, t, (T)1));
+    Ur[1][0] = -(c * (d[1] * T_FMA(dh, tanp, tana)));
+    Ur[0][1] = c * (d[0] * T_FMA(dh, tana, tanp));
+    Ur[1][1] = c * (d[1] * T_FMA(-tana, tanp, dh));
+    for (int i = 0; i < 2; ++i)              /* U = P_r (P_r* U) */
+        for (int j = 0; j < 2; ++j)
+            U[i][j] = Ur[pr ? 1 - i : i][j];
+
+    const T w = cosq * tanq;
+    T Vc[2][2];                              /* D~ V_psi */
+    Vc[0][0] = cosq;
+    Vc[0][1] = w;
+    Vc[1][0] = -(dt * w);
+    Vc[1][1] = dt * cosq;
+    for (int i = 0; i < 2; ++i)              /* V = P_c (D~ V_psi) */
+        for (int j = 0; j < 2; ++j)
+            V[i][j] = Vc[pc ? 1 - i : i][j];
+
+    *s_out = s;
+    *piv = pc | (pr << 1);
+}
+
+/*
+ * One complex 2x2 SVD, Sec. 2 (Eq. 1 - Eq. 29) as vectorized in Fig. 3 - Fig. 10,
+ * one lane at a time.  Ar/Ai hold the real and imaginary parts of a_{i+1,j+1}.
+ */
+static inline void SFX(svd2_cplx)(const T Ar[2][2], const T Ai[2][2],
+                           T Ur[2][2], T Ui[2][2], T Vr[2][2], T Vi[2][2],
+                           T *smax, T *smin, T *s_out, int *piv)
+{
+    /* Phase 1: Eq. 2 over the real and the imaginary parts (Fig. 3). */
+    const T parts[8] = { Ar[0][0], Ai[0][0], Ar[1][0], Ai[1][0],
+                         Ar[0][1], Ai[0][1], Ar[1][1], Ai[1][1] };
+    const T s = SFX(scale_exponent)(parts, 8);
+    T Ahr[2][2], Ahi[2][2], absAh[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            Ahr[i][j] = SFX(scalef)(Ar[i][j], s);
+            Ahi[i][j] = SFX(scalef)(Ai[i][j], s);
+            absAh[i][j] = SFX(hypot_naive)(Ahr[i][j], Ahi[i][j]);   /* Eq. 1, Fig. 4 */
+        }
+
+    /* Column norms (Eq. 3) and the column pivoting (Fig. 5). */
+    T nrm[2];
+    for (int j = 0; j < 2; ++j)
+        nrm[j] = SFX(hypot_naive)(absAh[0][j], absAh[1][j]);
+    const int pc = nrm[0] < nrm[1];
+    T A1r[2][2], A1i[2][2], absA1[2][2], nrm1[2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const int jj = pc ? 1 - j : j;
+            A1r[i][j] = Ahr[i][jj];
+            A1i[i][j] = Ahi[i][jj];
+            absA1[i][j] = absAh[i][jj];
+        }
+    nrm1[0] = nrm[pc ? 1 : 0];
+    nrm1[1] = nrm[pc ? 0 : 1];
+
+    /* Row sorting (Fig. 6). */
+    const int pr = absA1[0][0] < absA1[1][0];
+    T A2r[2][2], A2i[2][2], absA2[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const int ii = pr ? 1 - i : i;
+            A2r[i][j] = A1r[ii][j];
+            A2i[i][j] = A1i[ii][j];
+            absA2[i][j] = absA1[ii][j];
+        }
+
+    /* D* of Eq. 4 (Fig. 7): d_ii = e^{i arg a''_i1}; a'''_i1 = |a''_i1|;
+     * a'''_i2 = conj(d_ii) a''_i2 by the fma complex product of Eq. 5. */
+    T dr[2], di[2], A3r[2][2], A3i[2][2];
+    for (int i = 0; i < 2; ++i) {
+        SFX(cis_arg)(A2r[i][0], A2i[i][0], absA2[i][0], &dr[i], &di[i]);
+        A3r[i][1] = T_FMA(dr[i], A2r[i][1], di[i] * A2i[i][1]);
+        A3i[i][1] = T_FMA(dr[i], A2i[i][1], -(di[i] * A2r[i][1]));
+        A3r[i][0] = absA2[i][0];
+        A3i[i][0] = (T)0;
+    }
+
+    /* QR, Eq. 6 and Eq. 7 (Fig. 8). */
+    const T r11 = nrm1[0];
+    const T mtana = T_FMAX(A3r[1][0] / A3r[0][0], (T)0);
+    const T tana = -mtana;
+    const T cosa = SFX(invsqrt)(T_FMA(tana, tana, (T)1));
+    const T r12pr = cosa * T_FMA(mtana, A3r[1][1], A3r[0][1]);
+    const T r12pi = cosa * T_FMA(mtana, A3i[1][1], A3i[0][1]);
+    const T r22ppr = cosa * T_FMA(tana, A3r[0][1], A3r[1][1]);
+    const T r22ppi = cosa * T_FMA(tana, A3i[0][1], A3i[1][1]);
+
+    /* D~ of Eq. 8 (Fig. 9): r12 = |r'_12|; d~*_22 = e^{i arg r'_12};
+     * r'_22 = r''_22 d~_22 = r''_22 conj(d~*_22). */
+    const T r12 = SFX(hypot_naive)(r12pr, r12pi);
+    T dtsr, dtsi;
+    SFX(cis_arg)(r12pr, r12pi, r12, &dtsr, &dtsi);
+    const T r22pr = T_FMA(r22ppr, dtsr, r22ppi * dtsi);
+    const T r22pi = T_FMA(r22ppi, dtsr, -(r22ppr * dtsi));
+
+    /* D^* of Eq. 9 (Fig. 9): r22 = |r'_22|; d^_22 = e^{i arg r'_22}. */
+    const T r22 = SFX(hypot_naive)(r22pr, r22pi);
+    T dhr, dhi;
+    SFX(cis_arg)(r22pr, r22pi, r22, &dhr, &dhi);
+
+    /* Phase 3, Eq. 13 - Eq. 17 (Fig. 10); identical to the real case. */
+    const T x = T_FMAX(r12 / r11, (T)0);
+    const T y = T_FMAX(r22 / r11, (T)0);
+    const T num = ((T)2 * T_FMIN(x, y)) * T_FMAX(x, y);
+    const T den = T_FMA(x - y, x + y, (T)1);
+    const T tan2p = -T_FMIN(T_FMAX(num / den, (T)0), T_SQRT_MAX);
+    const T tanp = tan2p / ((T)1 + T_SQRT(T_FMA(tan2p, tan2p, (T)1)));
+    const T sec2p = T_FMA(tanp, tanp, (T)1);
+    const T cosp = SFX(invsqrt)(sec2p);
+    const T tanq = T_FMA(y, tanp, -x);
+    const T sec2q = T_FMA(tanq, tanq, (T)1);
+    const T cosq = SFX(invsqrt)(sec2q);
+    const T cpq = cosp * cosq;
+    *smax = (cpq * sec2q) * r11;
+    *smin = (cpq * sec2p) * r22;
+
+    /* Phase 4: the expansion of Eq. 29 printed after it.  Each element of
+     * P_r* U is c * (d_ii * w) with the inner value w, the complex product by
+     * Eq. 5, and the real factor c; the (2,1) element is negated. */
+    const T c = cosa * cosp;
+    const T t = -(tana * tanp);
+    T wr[2][2], wi[2][2];
+    wr[0][0] = T_FMA(dhr, t, (T)1);      wi[0][0] = dhi * t;
+    wr[1][0] = T_FMA(dhr, tanp, tana);   wi[1][0] = dhi * tanp;
+    wr[0][1] = T_FMA(dhr, tana, tanp);   wi[0][1] = dhi * tana;
+    wr[1][1] = T_FMA(-tana, tanp, dhr);  wi[1][1] = dhi;
+    T Prr[2][2], Pri[2][2];               /* P_r* U */
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const T pr_ = T_FMA(dr[i], wr[i][j], -(di[i] * wi[i][j]));
+            const T pi_ = T_FMA(dr[i], wi[i][j], di[i] * wr[i][j]);
+            const T sg = (i == 1 && j == 0) ? (T)-1 : (T)1;
+            Prr[i][j] = sg * (c * pr_);
+            Pri[i][j] = sg * (c * pi_);
+        }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            Ur[i][j] = Prr[pr ? 1 - i : i][j];
+            Ui[i][j] = Pri[pr ? 1 - i : i][j];
+        }
+
+    /* V = P_c D~ V_psi (Eq. 29), d~_22 = conj(d~*_22). */
+    const T w = cosq * tanq;
+    T Vcr[2][2], Vci[2][2];
+    Vcr[0][0] = cosq;          Vci[0][0] = (T)0;
+    Vcr[0][1] = w;             Vci[0][1] = (T)0;
+    Vcr[1][0] = -(dtsr * w);   Vci[1][0] = dtsi * w;
+    Vcr[1][1] = dtsr * cosq;   Vci[1][1] = -(dtsi * cosq);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            Vr[i][j] = Vcr[pc ? 1 - i : i][j];
+            Vi[i][j] = Vci[pc ? 1 - i : i][j];
+        }
+
+    *s_out = s;
+    *piv = pc | (pr << 1);
+}
+
+/*
+ * Reverse-mode derivative of A = U diag(s1, s2) V^T (real, s1 >= s2 >= 0) for a
+ * loss with gradients gU, gV (element order u11, u21, u12, u22) and g1, g2.  The
+ * paper has no backward; this is the square-SVD adjoint written out for order
+ * two (derivation in the design notes):
+ *   J = U^T gU, K = V^T gV, a = J12 - J21, b = K12 - K21,
+ *   M = [[g1, (a-b)/(2(s1+s2)) - (a+b)/(2(s1-s2))],
+ *        [-(a-b)/(2(s1+s2)) - (a+b)/(2(s1-s2)), g2]],
+ *   gA = U M V^T.
+ * 1/(s1 - s2) is safeguarded for nearly equal singular values: with the
+ * relative gap g = (s1 - s2)/s1 it is replaced by g / (s1 (g^2 + dl^2)), which
+ * is 1/(s1 - s2) for g >> dl and tends to 0 as g -> 0.  s1 + s2 = 0 (A = 0)
+ * gives 0 for both rotation terms.
+ */
+static inline void SFX(adjoint)(const T u[4], const T v[4], T s1, T s2, const T gu[4],
+                         const T gv[4], T g1, T g2, T dl, T ga[4])
+{
+    const T u11 = u[0], u21 = u[1], u12 = u[2], u22 = u[3];
+    const T v11 = v[0], v21 = v[1], v12 = v[2], v22 = v[3];
+    const T J12 = u11 * gu[2] + u21 * gu[3];
+    const T J21 = u12 * gu[0] + u22 * gu[1];
+    const T K12 = v11 * gv[2] + v21 * gv[3];
+    const T K21 = v12 * gv[0] + v22 * gv[1];
+    const T a = J12 - J21, b = K12 - K21;
+    const T sum = s1 + s2;
+    const T inv_sum = sum > (T)0 ? (T)1 / sum : (T)0;
+    T inv_gap = (T)0;
+    if (s1 > (T)0) {
+        const T g = (s1 - s2) / s1;
+        inv_gap = g / (s1 * (g * g + dl * dl));
+    }
+    const T p = (T)0.5 * (a - b) * inv_sum;
+    const T q = (T)0.5 * (a + b) * inv_gap;
+    const T m11 = g1, m12 = p - q, m21 = -p - q, m22 = g2;
+    /* W = U M, then gA = W V^T */
+    const T w11 = u11 * m11 + u12 * m21, w12 = u11 * m12 + u12 * m22;
+    const T w21 = u21 * m11 + u22 * m21, w22 = u21 * m12 + u22 * m22;
+    ga[0] = w11 * v11 + w12 * v12;   /* gA_11 */
+    ga[1] = w21 * v11 + w22 * v12;   /* gA_21 */
+    ga[2] = w11 * v21 + w12 * v22;   /* gA_12 */
+    ga[3] = w21 * v21 + w22 * v22;   /* gA_22 */
+}
