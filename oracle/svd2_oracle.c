@@ -44,8 +44,6 @@
 typedef __float128 quad;
 #define Q_FMA fmaq
 #define Q_SQRT sqrtq
-#define Q_FMIN fminq
-#define Q_FMAX fmaxq
 #define Q_FABS fabsq
 #define Q_COPYSIGN copysignq
 #define Q_LOGB logbq
@@ -58,8 +56,6 @@ typedef long double quad;
 _Static_assert(LDBL_MANT_DIG == 113, "AArch64 long double must be binary128");
 #define Q_FMA fmal
 #define Q_SQRT sqrtl
-#define Q_FMIN fminl
-#define Q_FMAX fmaxl
 #define Q_FABS fabsl
 #define Q_COPYSIGN copysignl
 #define Q_LOGB logbl
@@ -84,8 +80,6 @@ _Static_assert(LDBL_MANT_DIG == 113, "AArch64 long double must be binary128");
 #define T_SQRT_MAX 1.34078079299425956E+154
 #define T_FMA fma
 #define T_SQRT sqrt
-#define T_FMIN fmin
-#define T_FMAX fmax
 #define T_FABS fabs
 #define T_COPYSIGN copysign
 #define T_LOGB logb
@@ -99,8 +93,6 @@ _Static_assert(LDBL_MANT_DIG == 113, "AArch64 long double must be binary128");
 #undef T_SQRT_MAX
 #undef T_FMA
 #undef T_SQRT
-#undef T_FMIN
-#undef T_FMAX
 #undef T_FABS
 #undef T_COPYSIGN
 #undef T_LOGB
@@ -117,8 +109,6 @@ _Static_assert(LDBL_MANT_DIG == 113, "AArch64 long double must be binary128");
 #define T_SQRT_MAX sqrtf(FLT_MAX)
 #define T_FMA fmaf
 #define T_SQRT sqrtf
-#define T_FMIN fminf
-#define T_FMAX fmaxf
 #define T_FABS fabsf
 #define T_COPYSIGN copysignf
 #define T_LOGB logbf
@@ -132,8 +122,6 @@ _Static_assert(LDBL_MANT_DIG == 113, "AArch64 long double must be binary128");
 #undef T_SQRT_MAX
 #undef T_FMA
 #undef T_SQRT
-#undef T_FMIN
-#undef T_FMAX
 #undef T_FABS
 #undef T_COPYSIGN
 #undef T_LOGB
@@ -148,8 +136,6 @@ _Static_assert(LDBL_MANT_DIG == 113, "AArch64 long double must be binary128");
 #define T_SQRT_MAX Q_SQRT(Q_MAX)
 #define T_FMA Q_FMA
 #define T_SQRT Q_SQRT
-#define T_FMIN Q_FMIN
-#define T_FMAX Q_FMAX
 #define T_FABS Q_FABS
 #define T_COPYSIGN Q_COPYSIGN
 #define T_LOGB Q_LOGB

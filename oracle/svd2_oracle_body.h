@@ -15,16 +15,17 @@
  *   T_TRUE_MIN   smallest positive T        (DBL_TRUE_MIN in the paper, Eq. 1)
  *   T_MAX_EXP    T's MAX_EXP                (h = T_MAX_EXP - 3, Sec. 2.1)
  *   T_SQRT_MAX   RN(sqrt(T_MAX))            (bound in Eq. 14)
- *   T_FMA, T_SQRT, T_FMIN, T_FMAX, T_FABS, T_COPYSIGN, T_LOGB, T_SCALBN
+ *   T_FMA, T_SQRT, T_FABS, T_COPYSIGN, T_LOGB, T_SCALBN
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *  - hypot is the paper's own naive formula (Sec. 5, text before Fig. 4), so the
  *    result is a fixed sequence of correctly rounded operations;
  *  - invsqrt(x) = 1/sqrt(x) with IEEE sqrt and IEEE division (Sec. 6, the first
  *    remedy named before Fig. 8);
- *  - fmin/fmax are C's; every use below has a non-NaN constant second operand
- *    and no (+0,-0) pair can reach them, so C's semantics coincide with the
- *    relaxed ones of Sec. 2 (second argument returned for a NaN first);
+ *  - min/max are the relaxed fmin/fmax defined in Sec. 2 after Eq. 1 (the
+ *    VMINPD/VMAXPD semantics): pmin(a,b) = a < b ? a : b and pmax(a,b) =
+ *    a > b ? a : b, so a NaN first argument, or two zeros of either sign,
+ *    yield the second argument;
  *  - exp2 of Sec. 2.1 is logb (floor(lg|a|), exact for subnormals, -inf for 0);
  *    SCALEF is scalbn (round to nearest for subnormal results);
  *  - s stays a T as in Eq. 2, with T_MAX for the all-zero matrix;
@@ -36,15 +37,27 @@
  *    v21 = -d~22 (cos(psi) tan(psi)), v22 = d~22 cos(psi).
  */
 
+/* Sec. 2, the relaxed fmin and fmax defined after Eq. 1: the smaller (larger)
+ * of two non-NaN arguments, else the second argument. */
+static inline T SFX(pmin)(T a, T b)
+{
+    return a < b ? a : b;
+}
+
+static inline T SFX(pmax)(T a, T b)
+{
+    return a > b ? a : b;
+}
+
 /* ---- Sec. 2 and Sec. 5 (before Fig. 4): hypot(a,b) without exponent
  * adjustment.  a' = max(|a|,|b|), b' = min(|a|,|b|), a+ = max(a', TRUE_MIN),
  * q+ = b'/a+ <= 1, c = a' * sqrt(fma(q+, q+, 1)).  hypot(a,b) = 0 iff a = b = 0. */
 static inline T SFX(hypot_naive)(T a, T b)
 {
     T aa = T_FABS(a), ab = T_FABS(b);
-    T ap = T_FMAX(aa, ab);
-    T bp = T_FMIN(aa, ab);
-    T apl = T_FMAX(ap, T_TRUE_MIN);
+    T ap = SFX(pmax)(aa, ab);
+    T bp = SFX(pmin)(aa, ab);
+    T apl = SFX(pmax)(ap, T_TRUE_MIN);
     T q = bp / apl;
     return ap * T_SQRT(T_FMA(q, q, (T)1));
 }
@@ -62,8 +75,8 @@ static inline T SFX(invsqrt)(T x)
  * Im z / max(|z|, TRUE_MIN). */
 static inline void SFX(cis_arg)(T re, T im, T az, T *cr, T *ci)
 {
-    *cr = T_COPYSIGN(T_FMIN(T_FABS(re) / az, (T)1), re);
-    *ci = im / T_FMAX(az, T_TRUE_MIN);
+    *cr = T_COPYSIGN(SFX(pmin)(T_FABS(re) / az, (T)1), re);
+    *ci = im / SFX(pmax)(az, T_TRUE_MIN);
 }
 
 /* Sec. 2.1, Eq. 2 and Fig. 3: s = min{T_MAX, min_ij (h - exp2 part_ij)} over the
@@ -73,7 +86,7 @@ static inline T SFX(scale_exponent)(const T *part, int np)
     const T h = (T)(T_MAX_EXP - 3);
     T s = T_MAX;
     for (int k = 0; k < np; ++k)
-        s = T_FMIN(s, h - T_LOGB(part[k]));
+        s = SFX(pmin)(s, h - T_LOGB(part[k]));
     return s;
 }
 
@@ -143,7 +156,7 @@ static inline void SFX(svd2_real)(const T A[2][2], T U[2][2], T V[2][2],
     /* QR by the Givens rotation Q_alpha*, Eq. 6 and Eq. 7 (Fig. 8).  r11 is the
      * already known norm of the first column. */
     const T r11 = nrm1[0];
-    const T mtana = T_FMAX(A3[1][0] / A3[0][0], (T)0);      /* -tan(alpha) */
+    const T mtana = SFX(pmax)(A3[1][0] / A3[0][0], (T)0);      /* -tan(alpha) */
     const T tana = -mtana;
     const T cosa = SFX(invsqrt)(T_FMA(tana, tana, (T)1));
     const T r12p = cosa * T_FMA(mtana, A3[1][1], A3[0][1]);  /* r'_12 */
@@ -157,11 +170,11 @@ static inline void SFX(svd2_real)(const T A[2][2], T U[2][2], T V[2][2],
     const T r22 = T_FABS(r22p);
 
     /* Phase 3, Sec. 2.3: SVD of R, Eq. 13 - Eq. 17 (Fig. 10). */
-    const T x = T_FMAX(r12 / r11, (T)0);
-    const T y = T_FMAX(r22 / r11, (T)0);
-    const T num = ((T)2 * T_FMIN(x, y)) * T_FMAX(x, y);
+    const T x = SFX(pmax)(r12 / r11, (T)0);
+    const T y = SFX(pmax)(r22 / r11, (T)0);
+    const T num = ((T)2 * SFX(pmin)(x, y)) * SFX(pmax)(x, y);
     const T den = T_FMA(x - y, x + y, (T)1);
-    const T tan2p = -T_FMIN(T_FMAX(num / den, (T)0), T_SQRT_MAX);   /* Eq. 14 */
+    const T tan2p = -SFX(pmin)(SFX(pmax)(num / den, (T)0), T_SQRT_MAX);   /* Eq. 14 */
     const T tanp = tan2p / ((T)1 + T_SQRT(T_FMA(tan2p, tan2p, (T)1))); /* Eq. 15 */
     const T sec2p = T_FMA(tanp, tanp, (T)1);
     const T cosp = SFX(invsqrt)(sec2p);
@@ -260,7 +273,7 @@ static inline void SFX(svd2_cplx)(const T Ar[2][2], const T Ai[2][2],
 
     /* QR, Eq. 6 and Eq. 7 (Fig. 8). */
     const T r11 = nrm1[0];
-    const T mtana = T_FMAX(A3r[1][0] / A3r[0][0], (T)0);
+    const T mtana = SFX(pmax)(A3r[1][0] / A3r[0][0], (T)0);
     const T tana = -mtana;
     const T cosa = SFX(invsqrt)(T_FMA(tana, tana, (T)1));
     const T r12pr = cosa * T_FMA(mtana, A3r[1][1], A3r[0][1]);
@@ -282,11 +295,11 @@ static inline void SFX(svd2_cplx)(const T Ar[2][2], const T Ai[2][2],
     SFX(cis_arg)(r22pr, r22pi, r22, &dhr, &dhi);
 
     /* Phase 3, Eq. 13 - Eq. 17 (Fig. 10); identical to the real case. */
-    const T x = T_FMAX(r12 / r11, (T)0);
-    const T y = T_FMAX(r22 / r11, (T)0);
-    const T num = ((T)2 * T_FMIN(x, y)) * T_FMAX(x, y);
+    const T x = SFX(pmax)(r12 / r11, (T)0);
+    const T y = SFX(pmax)(r22 / r11, (T)0);
+    const T num = ((T)2 * SFX(pmin)(x, y)) * SFX(pmax)(x, y);
     const T den = T_FMA(x - y, x + y, (T)1);
-    const T tan2p = -T_FMIN(T_FMAX(num / den, (T)0), T_SQRT_MAX);
+    const T tan2p = -SFX(pmin)(SFX(pmax)(num / den, (T)0), T_SQRT_MAX);
     const T tanp = tan2p / ((T)1 + T_SQRT(T_FMA(tan2p, tan2p, (T)1)));
     const T sec2p = T_FMA(tanp, tanp, (T)1);
     const T cosp = SFX(invsqrt)(sec2p);

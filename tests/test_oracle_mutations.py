@@ -30,8 +30,10 @@ MUTATIONS = {
     "conj_dropped": ("A3i[i][1] = T_FMA(dr[i], A2i[i][1], -(di[i] * A2r[i][1]));",
                      "A3i[i][1] = T_FMA(dr[i], A2i[i][1], (di[i] * A2r[i][1]));"),
     "h_off_by_one": ("const T h = (T)(T_MAX_EXP - 3);", "const T h = (T)(T_MAX_EXP - 2);"),
-    "tan2phi_dropped_2": ("const T num = ((T)2 * T_FMIN(x, y)) * T_FMAX(x, y);",
-                          "const T num = T_FMIN(x, y) * T_FMAX(x, y);"),
+    "tan2phi_dropped_2": ("const T num = ((T)2 * SFX(pmin)(x, y)) * SFX(pmax)(x, y);",
+                          "const T num = SFX(pmin)(x, y) * SFX(pmax)(x, y);"),
+    "alpha_quotient_inverted": ("const T mtana = SFX(pmax)(A3[1][0] / A3[0][0], (T)0);",
+                                "const T mtana = SFX(pmax)(A3[0][0] / A3[1][0], (T)0);"),
     "u_cmul_sign": ("const T pi_ = T_FMA(dr[i], wi[i][j], di[i] * wr[i][j]);",
                     "const T pi_ = T_FMA(dr[i], wi[i][j], -(di[i] * wr[i][j]));"),
     "real_dstar_dropped": ("A3[i][1] = d[i] * A2[i][1];", "A3[i][1] = A2[i][1];"),
