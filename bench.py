@@ -1,0 +1,281 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched 2x2 SVD library on one node.
+
+A step is one pass of the whole hot path -- scaling (Eq. 2), URV (Eq. 4 -
+Eq. 11), SVD of R (Eq. 13 - Eq. 17), assembly of U and V (Eq. 29) and the
+stores -- over one batch of synthetic input.  The default workload is the
+complex128 batch of n = 2^24 matrices (real and imaginary parts uniform in
+[-1, 1] times 2^e, e uniform in [-500, 500] per matrix, 1% rank-deficient),
+generated by the seeded generator in ``paper_2005_07403_gb300.inputs`` and
+resident in HBM before the timed region.  Its 1 GiB of input (3.3 GiB moved
+per step) is far larger than the 129 MB L2, so no flush is needed between
+steps.
+
+Multi-GPU (torchrun): every rank processes its own batch of the same size
+(independent problems, weak scaling); there is no data-path collective, only a
+barrier and a max-reduction of the timing.
+
+``--impl reference`` times the CPU oracle (the step-by-step scalar method in
+plain C, OpenMP over the host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2x2 SVDs/sec and achieved HBM GB/s vs peak, FP64 vs FP32 at stated error"
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per matrix: one read of A, one write of U, V, Sigma', s (int32).
+WORKLOADS = {
+    "complex128": dict(rows=8, dtype="float64", n=2**24, bytes_per=64 + 64 + 64 + 8 + 8 + 4,
+                       kind="z",
+                       desc="complex128 n=2^24, parts U[-1,1]*2^e, e in [-500,500] per matrix, "
+                            "1% rank-deficient"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="complex128")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smmax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smmax) if smmax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(A, rows, min_seconds=10.0, sample=2**21):
+    """The oracle as it stands, on all host cores, over a bounded sample of the
+    workload (the first `sample` matrices), repeated for at least min_seconds."""
+    import oracle
+    S = np.ascontiguousarray(A[:, :sample])
+    oracle.svd2(S[:, :1024])          # build/load outside the timing
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.svd2(S)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": reps * S.shape[1] / el, "unit": "matrices/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"first {S.shape[1]} matrices of the workload, {reps} passes, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2005_07403_gb300 import inputs
+    W = WORKLOADS[args.workload]
+    sample = 2**21
+    A = inputs.complex_scaled(sample)
+    oracle.svd2(A[:, :1024].copy())
+    for _ in range(args.warmup):
+        oracle.svd2(A)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.svd2(A)
+    el = time.perf_counter() - t0
+    value = args.steps * sample / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["desc"], "sample_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": "matrices/s", "kind": "oracle",
+                             "cores": oracle.max_threads(),
+                             "sample": f"{sample} matrices of the workload per step"},
+            "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2005_07403_gb300 import inputs
+    from paper_2005_07403_gb300 import svd2 as S
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS[args.workload]
+    n = W["n"]
+    A = inputs.complex_scaled(n, seed=inputs.SEED_CFG2 + rank)
+    Ad = torch.from_numpy(A).cuda()
+    out = S.empty_result(W["rows"], n, Ad.dtype, Ad.device)
+    S.lib()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        S.svd2(Ad, out=out)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        S.svd2(Ad, out=out)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * n * args.steps / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: H2D of A, the call,
+    # D2H of every output, each step
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(A).pin_memory()
+        outs_h = [torch.empty(t.shape, dtype=t.dtype).pin_memory()
+                  for t in (out.U, out.V, out.smax, out.smin, out.s)]
+        h2d = Ah.numel() * Ah.element_size()
+        d2h = sum(t.numel() * t.element_size() for t in outs_h)
+        ke = max(2, min(args.steps, 5))
+        for it in range(ke + 1):
+            if it == 1:
+                barrier()
+                e0.record(stream)
+            Ad.copy_(Ah, non_blocking=True)
+            S.svd2(Ad, out=out)
+            for th, td in zip(outs_h, (out.U, out.V, out.smax, out.smin, out.s)):
+                th.copy_(td, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        et = torch.tensor([ems], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * n * ke / (float(et.item()) / 1e3), "unit": "matrices/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peak, peak_src = measured_peaks()
+    bytes_launch = W["bytes_per"] * n
+    achieved = bytes_launch / (ms_per_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": f"peak {peak_src}; algorithmic {W['bytes_per']} B/matrix x {n} per launch"}
+    line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": W["desc"], "n_per_gpu": n, "l2": "inputs larger than L2 (1 GiB)",
+                       "launch": S.get_launch(W["kind"])},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, W["rows"])
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

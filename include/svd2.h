@@ -1,0 +1,109 @@
+/*
+ * svd2.h -- C ABI of the GB300 (sm_103a) batched 2x2 SVD library.
+ *
+ * Computes, for n independent real or complex 2x2 matrices A, the SVD
+ * A = U Sigma V^* by the method of V. Novakovic, "Batched computation of the
+ * singular value decompositions of order two by the AVX-512 vectorization"
+ * (arXiv 2005.07403): exact power-of-two scaling (Sec. 2.1, Eq. 2), the URV
+ * factorization (Sec. 2.2, Eq. 4 - Eq. 11), the SVD of the non-negative upper
+ * triangular middle factor (Sec. 2.3, Eq. 12 - Eq. 17) and the assembly of U
+ * and V (Eq. 28, Eq. 29).  This is the annihilation step of one parallel
+ * Kogbetliantz sweep (Sec. 1).
+ *
+ * Data layout (Sec. 3): the split layout.  Each matrix element has its own
+ * contiguous array of n values, the real and imaginary parts of complex
+ * elements in separate arrays.  Element arrays are passed as a HOST array of
+ * DEVICE pointers, in the record order of Sec. 8:
+ *   real    (4): a11, a21, a12, a22
+ *   complex (8): Re a11, Im a11, Re a21, Im a21, Re a12, Im a12, Re a22, Im a22
+ * U and V use the same order as A.  smax, smin and s are arrays of n values.
+ * All device arrays are caller-owned (the library never frees them), must be
+ * distinct from each other (outputs must not alias inputs or each other) and
+ * may have any alignment of their element type; 16-byte aligned arrays take
+ * vectorised loads and stores.
+ *
+ * Outputs (Sec. 2.3, Fig. 1): by default smax, smin hold the scaled singular
+ * values Sigma' (sigma'_max >= sigma'_min >= 0, always finite for finite
+ * input, Theorem 1) and s holds the scale exponent of Eq. 2, so that
+ * Sigma = 2^-s Sigma'.  The zero matrix has s = SVD2_S_ZERO (the paper's
+ * s = DBL_MAX).  With SVD2_BACKSCALE the library stores Sigma = 2^-s Sigma'
+ * (correctly rounded; it may overflow or underflow, Sec. 2.3) and s = 0.
+ *
+ * Preconditions and errors: inputs must be finite (Sec. 1); non-finite input
+ * gives unspecified values but never a fault or a hang.  All entry points are
+ * asynchronous on the given stream (NULL = the legacy default stream) and
+ * return SVD2_OK, or a negative code: SVD2_EINVAL for a bad argument (n < 0, a
+ * NULL array with n > 0, unknown flags), SVD2_ECUDA when a CUDA call failed
+ * (its cudaError_t is kept per thread for svd2_last_cuda_error()).  n == 0 is
+ * a no-op.  Inputs are never modified.
+ */
+#ifndef SVD2_H
+#define SVD2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so the header needs no CUDA headers. */
+typedef struct CUstream_st *svd2_stream_t;
+
+#define SVD2_OK 0
+#define SVD2_EINVAL (-1)
+#define SVD2_ECUDA (-2)
+#define SVD2_ENOMEM (-3)
+
+#define SVD2_S_ZERO INT32_MAX      /* s of the all-zero matrix (Eq. 2: s = DBL_MAX) */
+#define SVD2_BACKSCALE 1u          /* store Sigma = 2^-s Sigma' and s = 0 (Fig. 1)  */
+
+/*
+ * Real FP64: n matrices.  A[4], U[4], V[4] hold device pointers to n doubles
+ * each; smax, smin: n doubles; s: n int32.  Sec. 2 with the real forms of
+ * Eq. 10; every step is a correctly rounded IEEE double operation in the
+ * paper's order, so the results are those of the step-by-step method.
+ */
+int svd2_batch_d(int64_t n, const double *const A[4], double *const U[4],
+                 double *const V[4], double *smax, double *smin, int32_t *s,
+                 uint32_t flags, svd2_stream_t stream);
+
+/* Complex FP64 (complex128 split into real and imaginary parts): A[8], U[8],
+ * V[8] of n doubles each.  Sec. 2, Eq. 1 - Eq. 29, Fig. 3 - Fig. 10. */
+int svd2_batch_z(int64_t n, const double *const A[8], double *const U[8],
+                 double *const V[8], double *smax, double *smin, int32_t *s,
+                 uint32_t flags, svd2_stream_t stream);
+
+/* Real FP32: the single-precision variant of Sec. 1 and Sec. 7 (FLT_*
+ * constants, h = FLT_MAX_EXP - 3 = 125, tan(2 phi) bounded by sqrt(FLT_MAX)). */
+int svd2_batch_s(int64_t n, const float *const A[4], float *const U[4],
+                 float *const V[4], float *smax, float *smin, int32_t *s,
+                 uint32_t flags, svd2_stream_t stream);
+
+/* Complex FP32 (complex64 split into parts); as svd2_batch_z in single precision. */
+int svd2_batch_c(int64_t n, const float *const A[8], float *const U[8],
+                 float *const V[8], float *smax, float *smin, int32_t *s,
+                 uint32_t flags, svd2_stream_t stream);
+
+/*
+ * Launch shape of the forward kernels.  op: 0 = d, 1 = z, 2 = s, 3 = c.
+ * block: threads per block (a multiple of 32, 32..512); mpt: matrices per
+ * thread per load (1, 2 or 4); unroll: load groups in flight per thread (1 or
+ * 2); waves: resident-grid multiples (grid = waves x SMs x resident blocks per
+ * SM, capped by the work; 0 = as many blocks as the work needs).  The setting
+ * is process-wide and applies to later calls.  Returns SVD2_EINVAL for an
+ * unsupported shape.
+ */
+int svd2_set_launch(int op, int block, int mpt, int unroll, int waves);
+int svd2_get_launch(int op, int *block, int *mpt, int *unroll, int *waves);
+
+/* The cudaError_t of the last failed CUDA call made by this thread (0 if none). */
+int svd2_last_cuda_error(void);
+
+/* Library version string. */
+const char *svd2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVD2_H */

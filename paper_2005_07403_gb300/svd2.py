@@ -1,0 +1,152 @@
+"""Thin Python binding of the C ABI in ``include/svd2.h`` (argument marshalling only).
+
+Every step of the method runs in the sm_103a kernels of the shared library
+built from ``csrc/``; torch only provides device memory and the current CUDA
+stream.  There is no CPU fallback: if the library cannot be built or loaded,
+or no CUDA device is present, the calls raise.
+
+Arrays follow the split layout of Sec. 3: a tensor of shape (4, n) (real) or
+(8, n) (complex, real and imaginary parts in separate rows) whose rows are the
+element arrays in the record order of Sec. 8 -- a11, a21, a12, a22, or
+Re a11, Im a11, Re a21, Im a21, Re a12, Im a12, Re a22, Im a22.  Each row must
+be contiguous; rows need not be adjacent.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+OK = 0
+EINVAL = -1
+ECUDA = -2
+ENOMEM = -3
+S_ZERO = 2**31 - 1
+BACKSCALE = 1
+
+OPS = {"d": 0, "z": 1, "s": 2, "c": 3}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Svd2Error(RuntimeError):
+    pass
+
+
+def lib():
+    """Load (building first if sources changed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    P = ctypes.c_void_p
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    for name in ("svd2_batch_d", "svd2_batch_z", "svd2_batch_s", "svd2_batch_c"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_uint32, P]
+        f.restype = ctypes.c_int
+    L.svd2_set_launch.argtypes = [ctypes.c_int] * 5
+    L.svd2_set_launch.restype = ctypes.c_int
+    L.svd2_get_launch.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4
+    L.svd2_get_launch.restype = ctypes.c_int
+    L.svd2_last_cuda_error.restype = ctypes.c_int
+    L.svd2_version.restype = ctypes.c_char_p
+
+
+def check(rc: int, what: str):
+    if rc != OK:
+        err = lib().svd2_last_cuda_error()
+        raise Svd2Error(f"{what} failed with code {rc} (cudaError {err})")
+
+
+def ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+def current_stream_handle(device=None) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _kind(rows: int, dtype: torch.dtype) -> str:
+    if dtype == torch.float64:
+        return {4: "d", 8: "z"}[rows]
+    if dtype == torch.float32:
+        return {4: "s", 8: "c"}[rows]
+    raise TypeError(f"unsupported dtype {dtype}")
+
+
+@dataclass
+class Svd2Result:
+    U: torch.Tensor      # (rows, n), element order of A
+    V: torch.Tensor      # (rows, n)
+    smax: torch.Tensor   # (n,) sigma'_max (or sigma_max with backscale)
+    smin: torch.Tensor   # (n,)
+    s: torch.Tensor      # (n,) int32 scale exponents (Eq. 2); S_ZERO for A = 0
+
+
+def _rows(t: torch.Tensor, what: str):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if t.dim() != 2 or t.shape[0] not in (4, 8):
+        raise ValueError(f"{what} must have shape (4, n) or (8, n)")
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError(f"{what}: each row must be contiguous")
+    return [t[i].data_ptr() for i in range(t.shape[0])]
+
+
+def empty_result(rows: int, n: int, dtype, device) -> Svd2Result:
+    return Svd2Result(
+        U=torch.empty((rows, n), dtype=dtype, device=device),
+        V=torch.empty((rows, n), dtype=dtype, device=device),
+        smax=torch.empty(n, dtype=dtype, device=device),
+        smin=torch.empty(n, dtype=dtype, device=device),
+        s=torch.empty(n, dtype=torch.int32, device=device))
+
+
+def svd2(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = None,
+         stream: int | None = None) -> Svd2Result:
+    """Batched 2x2 SVD of the split-layout batch ``A`` (shape (4, n) or (8, n),
+    float64 or float32, on a CUDA device).  Asynchronous on ``stream`` (default:
+    torch's current stream)."""
+    rows, n = A.shape
+    kind = _kind(rows, A.dtype)
+    a_ptrs = _rows(A, "A")
+    if out is None:
+        out = empty_result(rows, n, A.dtype, A.device)
+    u_ptrs = _rows(out.U, "U")
+    v_ptrs = _rows(out.V, "V")
+    h = current_stream_handle(A.device) if stream is None else stream
+    f = getattr(lib(), "svd2_batch_" + kind)
+    rc = f(n, ptr_array(a_ptrs), ptr_array(u_ptrs), ptr_array(v_ptrs), out.smax.data_ptr(),
+           out.smin.data_ptr(), out.s.data_ptr(), BACKSCALE if backscale else 0, h)
+    check(rc, "svd2_batch_" + kind)
+    return out
+
+
+def set_launch(kind: str, block: int, mpt: int, unroll: int, waves: int = 0):
+    check(lib().svd2_set_launch(OPS[kind], block, mpt, unroll, waves), "svd2_set_launch")
+
+
+def get_launch(kind: str):
+    vals = [ctypes.c_int() for _ in range(4)]
+    check(lib().svd2_get_launch(OPS[kind], *[ctypes.byref(v) for v in vals]), "svd2_get_launch")
+    return tuple(v.value for v in vals)
+
+
+def version() -> str:
+    return lib().svd2_version().decode()

@@ -1,0 +1,190 @@
+"""Parity of the CUDA forward kernels with the CPU oracle, element by element.
+
+Every step of both sides is a correctly rounded IEEE operation in the paper's
+order, so the kernels must reproduce the oracle bit for bit (signed zeros
+included): this is stricter than the stated bar (s exact, sigma within 4 ulp,
+backward error <= 8 eps ||A||_F), which the oracle itself meets (see the oracle
+pins).  Inputs come from the seeded generators; sizes span many blocks and a
+ragged tail; the full-size workloads are checked on sampled matrices.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2005_07403_gb300 import inputs
+from paper_2005_07403_gb300 import svd2 as S
+from tests.helpers import bits_equal
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_svd2(A, backscale=False, row_offset=0):
+    """Run the kernel on numpy batch A; row_offset > 0 places every array at an
+    element offset (misaligned for vector loads)."""
+    rows, n = A.shape
+    dt = torch.float64 if A.dtype == np.float64 else torch.float32
+    if row_offset:
+        buf = torch.empty((rows, n + row_offset), dtype=dt, device="cuda")
+        buf[:, row_offset:] = torch.from_numpy(A).cuda()
+        Ad = buf[:, row_offset:]
+        out = S.Svd2Result(
+            U=torch.empty((rows, n + row_offset), dtype=dt, device="cuda")[:, row_offset:],
+            V=torch.empty((rows, n + row_offset), dtype=dt, device="cuda")[:, row_offset:],
+            smax=torch.empty(n + row_offset, dtype=dt, device="cuda")[row_offset:],
+            smin=torch.empty(n + row_offset, dtype=dt, device="cuda")[row_offset:],
+            s=torch.empty(n + row_offset, dtype=torch.int32, device="cuda")[row_offset:])
+    else:
+        Ad = torch.from_numpy(A).cuda()
+        out = None
+    r = S.svd2(Ad, backscale=backscale, out=out)
+    torch.cuda.synchronize()
+    return {k: getattr(r, k).cpu().numpy() for k in ("U", "V", "smax", "smin", "s")}
+
+
+def assert_same(g, o, what=""):
+    for k in ("U", "V", "smax", "smin"):
+        if not bits_equal(g[k], o[k]):
+            bad = np.nonzero((g[k] != o[k]) & ~(np.isnan(g[k]) & np.isnan(o[k])))
+            raise AssertionError(f"{what}: {k} differs at {bad[-1][:8]} ({len(bad[-1])} values)")
+    assert np.array_equal(g["s"], o["s"]), what
+
+
+def check(A, what, backscale=False, **kw):
+    g = gpu_svd2(A, backscale=backscale, **kw)
+    with np.errstate(all="ignore"):
+        o = oracle.svd2(A, backscale=backscale)
+    assert_same(g, o, what)
+
+
+# ------------------------------------------------------------------ FP64
+
+def test_real_mixed_workload():
+    """The real FP64 workload: n = 65536 mixed classes (zero, diagonal,
+    upper-triangular, rank-1, 2^e-scaled entries among N(0,1) matrices)."""
+    check(inputs.real_mixed(65536), "real_mixed")
+
+
+def test_real_ragged_tail_and_random_bits():
+    check(inputs.real_mixed(65536 + 37, seed=7), "real_mixed+37")
+    check(inputs.random_bits(2**16 + 3, 4, 11), "rbits")
+
+
+def test_real_edge_cases():
+    check(inputs.edge_real(), "edge")
+    check(np.ascontiguousarray(np.repeat(inputs.edge_real(), 33, axis=1)), "edge x33")
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 31, 33, 255, 257])
+def test_small_n(n):
+    check(inputs.normal_batch(n, 4, 100 + n), f"d n={n}")
+    check(inputs.normal_batch(n, 8, 200 + n), f"z n={n}")
+    check(inputs.normal_batch(n, 4, 300 + n, np.float32), f"s n={n}")
+    check(inputs.normal_batch(n, 8, 400 + n, np.float32), f"c n={n}")
+
+
+def test_complex_workload_small():
+    check(inputs.complex_scaled(2**16 + 5), "complex_scaled")
+    check(inputs.random_bits(2**15 + 1, 8, 12), "crbits")
+    check(inputs.normal_batch(2**15, 8, 13), "cnormal")
+
+
+def test_complex_with_real_values():
+    Ar = inputs.edge_real()
+    Ac = np.zeros((8, Ar.shape[1]))
+    Ac[0::2] = Ar
+    check(Ac, "complex edge")
+
+
+# ------------------------------------------------------------------ FP32
+
+def test_fp32_real_and_complex():
+    check(inputs.normal_batch(2**16 + 3, 4, 21, np.float32), "s normal")
+    check(inputs.random_bits_f32(2**16, 4, 22), "s rbits")
+    check(inputs.edge_real(np.float32), "s edge")
+    A32, _ = inputs.real_fp32_illcond(2**16)
+    check(A32, "s illcond")
+    check(inputs.normal_batch(2**15 + 1, 8, 23, np.float32), "c normal")
+    check(inputs.random_bits_f32(2**15, 8, 24), "c rbits")
+
+
+# ----------------------------------------------------------- options/shapes
+
+def test_backscale_flag():
+    """Fig. 1: Sigma = 2^-s Sigma' correctly rounded (overflow to inf allowed) and s = 0."""
+    check(inputs.random_bits(2**14, 4, 31), "d backscale", backscale=True)
+    check(inputs.random_bits(2**14, 8, 32), "z backscale", backscale=True)
+    check(inputs.random_bits_f32(2**14, 4, 33), "s backscale", backscale=True)
+    check(inputs.edge_real(), "edge backscale", backscale=True)
+
+
+LAUNCHES = [(32, 1, 1, 0), (64, 2, 2, 1), (128, 4, 1, 2), (512, 4, 2, 0), (256, 1, 2, 1),
+            (96, 2, 1, 3)]
+
+
+@pytest.mark.parametrize("shape", LAUNCHES)
+def test_launch_shapes_do_not_change_results(shape):
+    A = {"d": inputs.real_mixed(40000 + 3, seed=5), "z": inputs.complex_scaled(20000 + 1),
+         "s": inputs.normal_batch(40000 + 2, 4, 6, np.float32),
+         "c": inputs.normal_batch(20000 + 3, 8, 7, np.float32)}
+    saved = {k: S.get_launch(k) for k in A}
+    try:
+        for k, a in A.items():
+            S.set_launch(k, *shape)
+            check(a, f"{k} {shape}")
+    finally:
+        for k, v in saved.items():
+            S.set_launch(k, *v)
+
+
+def test_misaligned_arrays_take_the_scalar_path():
+    check(inputs.real_mixed(10001), "d offset", row_offset=1)
+    check(inputs.normal_batch(5003, 8, 41, np.float32), "c offset", row_offset=3)
+
+
+def test_output_guard_bands_untouched():
+    """Canaries after every output array (in place of a memory checker)."""
+    n, pad = 10007, 64
+    A = torch.from_numpy(inputs.normal_batch(n, 8, 51)).cuda()
+    canary = float.fromhex("0x1.dead0p+7")
+    bufs = [torch.full((8, n + pad), canary, dtype=torch.float64, device="cuda") for _ in range(2)]
+    sb = [torch.full((n + pad,), canary, dtype=torch.float64, device="cuda") for _ in range(2)]
+    si = torch.full((n + pad,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    out = S.Svd2Result(U=bufs[0][:, :n], V=bufs[1][:, :n], smax=sb[0][:n], smin=sb[1][:n], s=si[:n])
+    S.svd2(A, out=out)
+    torch.cuda.synchronize()
+    for b in bufs:
+        assert torch.all(b[:, n:] == canary)
+    for b in sb:
+        assert torch.all(b[n:] == canary)
+    assert torch.all(si[n:] == 0x5A5A5A5A)
+
+
+def test_zero_length_is_noop():
+    A = torch.empty((4, 0), dtype=torch.float64, device="cuda")
+    r = S.svd2(A)
+    assert r.U.shape == (4, 0)
+
+
+# ------------------------------------------------------ full-size, sampled
+
+def _sampled_check(A, what, nsample=1 << 15, seed=0):
+    g = S.svd2(torch.from_numpy(A).cuda())
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(seed).choice(A.shape[1], nsample, replace=False))
+    idx_t = torch.from_numpy(idx).cuda()
+    gs = {k: getattr(g, k).index_select(-1, idx_t).cpu().numpy()
+          for k in ("U", "V", "smax", "smin", "s")}
+    o = oracle.svd2(np.ascontiguousarray(A[:, idx]))
+    assert_same(gs, o, what)
+
+
+def test_full_size_complex_workload_sampled():
+    """The complex128 workload at its full size n = 2^24, in the launch shape
+    the benchmark uses, on 2^15 sampled matrices."""
+    _sampled_check(inputs.complex_scaled(2**24), "complex 2^24")
+
+
+def test_full_size_fp32_workload_sampled():
+    A32, _ = inputs.real_fp32_illcond(2**26)
+    _sampled_check(A32, "fp32 2^26")
