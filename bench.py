@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="complex128")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--n", type=int, default=0,
+                   help="override the batch size (small cases for profiling only)")
     return p.parse_args()
 
 
@@ -186,7 +188,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     W = WORKLOADS[args.workload]
-    n = W["n"]
+    n = args.n or W["n"]
     A = inputs.complex_scaled(n, seed=inputs.SEED_CFG2 + rank)
     Ad = torch.from_numpy(A).cuda()
     out = S.empty_result(W["rows"], n, Ad.dtype, Ad.device)

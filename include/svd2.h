@@ -40,6 +40,7 @@
 #ifndef SVD2_H
 #define SVD2_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -83,6 +84,41 @@ int svd2_batch_s(int64_t n, const float *const A[4], float *const U[4],
 int svd2_batch_c(int64_t n, const float *const A[8], float *const U[8],
                  float *const V[8], float *smax, float *smin, int32_t *s,
                  uint32_t flags, svd2_stream_t stream);
+
+/*
+ * FP32 form with FP64 re-run.  The single-precision method (as svd2_batch_s /
+ * svd2_batch_c) runs over all n matrices; every matrix whose scaled singular
+ * values satisfy sigma'_min < 2^tau_log2 * sigma'_max (compared in float, the
+ * product by the power of two being exact) is decomposed again by the
+ * double-precision method on its exactly widened elements, and its float
+ * outputs are replaced by the double results rounded to nearest float, with
+ * sigma' on the float run's scale: sigma'_32 = RN(sigma'_64 * 2^(s32 - s64)).
+ * s is the float run's exponent (h = 125).  The tangent and cosine
+ * computations of Eq. 6 - Eq. 16 are where single precision loses the
+ * small singular value of an ill-conditioned matrix (sigma'_min carries about
+ * u * sigma'_max / sigma'_min relative error from r''_22, Fig. 8); a kept
+ * matrix has sigma'_min / sigma'_max >= 2^tau_log2, bounding that error.
+ * tau_log2 in [-100, 0]; the library's measured default is SVD2_RERUN_TAU_LOG2.
+ * workspace: device memory of at least svd2_rerun_workspace_bytes(n) bytes,
+ * 16-byte aligned, caller-owned, used by this call only (two calls sharing a
+ * workspace must be ordered on one stream).  After the call completes, its
+ * first 8 bytes hold the number of re-run matrices (uint64), see
+ * svd2_rerun_count.  flags as for svd2_batch_s (SVD2_BACKSCALE applies Fig. 1
+ * to the final float results).  Errors as above.
+ */
+#define SVD2_RERUN_TAU_LOG2 (-8)
+size_t svd2_rerun_workspace_bytes(int64_t n);
+int svd2_batch_s_rerun(int64_t n, const float *const A[4], float *const U[4],
+                       float *const V[4], float *smax, float *smin, int32_t *s,
+                       int tau_log2, uint32_t flags, void *workspace,
+                       size_t workspace_bytes, svd2_stream_t stream);
+int svd2_batch_c_rerun(int64_t n, const float *const A[8], float *const U[8],
+                       float *const V[8], float *smax, float *smin, int32_t *s,
+                       int tau_log2, uint32_t flags, void *workspace,
+                       size_t workspace_bytes, svd2_stream_t stream);
+/* Number of matrices re-run by the last call that used `workspace` (a device
+ * pointer); synchronous: call it once that call has completed. */
+int svd2_rerun_count(const void *workspace, int64_t *count);
 
 /*
  * Launch shape of the forward kernels.  op: 0 = d, 1 = z, 2 = s, 3 = c.

@@ -90,7 +90,8 @@ def _declare(lib):
         f.restype = None
     for name in ("svd2o_batch_s_rerun", "svd2o_batch_c_rerun"):
         f = getattr(lib, name)
-        f.argtypes = [_I64, pp, pp, pp, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int]
+        f.argtypes = [_I64, pp, pp, pp, _P, _P, _P, _P, ctypes.c_int, ctypes.c_uint32,
+                      ctypes.c_int]
         f.restype = _I64
     for name in ("svd2o_truth_d", "svd2o_truth_z"):
         f = getattr(lib, name)
@@ -174,7 +175,7 @@ class Oracle:
         return dict(U=U, V=V, smax=smax, smin=smin, s=s, piv=piv)
 
 
-    def svd2_rerun(self, A, tau_log2: int, *, nthreads: int = 0):
+    def svd2_rerun(self, A, tau_log2: int, *, backscale: bool = False, nthreads: int = 0):
         """FP32 form with FP64 re-run of the matrices with sigma'_min < 2^tau_log2 sigma'_max.
 
         ``A`` is float32 of shape (4, n) or (8, n).  Returns the dict of ``svd2``
@@ -194,7 +195,7 @@ class Oracle:
         lib = self.lib
         f = lib.svd2o_batch_s_rerun if rows == 4 else lib.svd2o_batch_c_rerun
         cnt = f(n, _ptrs(A), _ptrs(U), _ptrs(V), _p(smax), _p(smin), _p(s), _p(flagged),
-                int(tau_log2), nthreads)
+                int(tau_log2), BACKSCALE if backscale else 0, nthreads)
         return dict(U=U, V=V, smax=smax, smin=smin, s=s, flagged=flagged, count=int(cnt))
 
 
@@ -307,8 +308,8 @@ def svd2(A, *, backscale: bool = False, nthreads: int = 0):
     return _default().svd2(A, backscale=backscale, nthreads=nthreads)
 
 
-def svd2_rerun(A, tau_log2: int, *, nthreads: int = 0):
-    return _default().svd2_rerun(A, tau_log2, nthreads=nthreads)
+def svd2_rerun(A, tau_log2: int, *, backscale: bool = False, nthreads: int = 0):
+    return _default().svd2_rerun(A, tau_log2, backscale=backscale, nthreads=nthreads)
 
 
 def truth(A, s=None):

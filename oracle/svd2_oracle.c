@@ -295,11 +295,22 @@ void svd2o_batch_c(int64_t n, const float *const A[8], float *const U[8],
  * decomposed again by the double method on its exactly upcast elements; its
  * float outputs are then the double results rounded to float, with sigma'
  * brought to the float run's scale: sigma'_32 = RN32(sigma'_64 * 2^(s32 - s64)).
- * flagged[k] (may be NULL) receives 1 for re-run matrices.  Returns the count.
+ * flagged[k] (may be NULL) receives 1 for re-run matrices.  With
+ * SVD2O_BACKSCALE in flags, Fig. 1 is applied to these final float results
+ * (sigma = 2^-s sigma'_32 in float, then s = 0).  Returns the count.
  */
+static void backscale_f(float *sx, float *sn, int32_t *s)
+{
+    if (*s != ZERO_S) {
+        *sx = scalbnf(*sx, -*s);
+        *sn = scalbnf(*sn, -*s);
+    }
+    *s = 0;
+}
+
 int64_t svd2o_batch_s_rerun(int64_t n, const float *const A[4], float *const U[4],
                             float *const V[4], float *smax, float *smin, int32_t *s,
-                            uint8_t *flagged, int tau_log2, int nthreads)
+                            uint8_t *flagged, int tau_log2, uint32_t flags, int nthreads)
 {
     set_threads(nthreads);
     int64_t count = 0;
@@ -329,7 +340,10 @@ int64_t svd2o_batch_s_rerun(int64_t n, const float *const A[4], float *const U[4
         }
         U[0][k] = u[0][0]; U[1][k] = u[1][0]; U[2][k] = u[0][1]; U[3][k] = u[1][1];
         V[0][k] = v[0][0]; V[1][k] = v[1][0]; V[2][k] = v[0][1]; V[3][k] = v[1][1];
-        smax[k] = sx; smin[k] = sn; s[k] = s32;
+        int32_t so = s32;
+        if (flags & SVD2O_BACKSCALE)
+            backscale_f(&sx, &sn, &so);
+        smax[k] = sx; smin[k] = sn; s[k] = so;
         if (flagged) flagged[k] = (uint8_t)flag;
     }
     return count;
@@ -338,7 +352,7 @@ int64_t svd2o_batch_s_rerun(int64_t n, const float *const A[4], float *const U[4
 /* Complex counterpart of svd2o_batch_s_rerun. */
 int64_t svd2o_batch_c_rerun(int64_t n, const float *const A[8], float *const U[8],
                             float *const V[8], float *smax, float *smin, int32_t *s,
-                            uint8_t *flagged, int tau_log2, int nthreads)
+                            uint8_t *flagged, int tau_log2, uint32_t flags, int nthreads)
 {
     set_threads(nthreads);
     int64_t count = 0;
@@ -378,7 +392,10 @@ int64_t svd2o_batch_c_rerun(int64_t n, const float *const A[8], float *const U[8
                 U[e][k] = ur[i][j]; U[e + 1][k] = ui[i][j];
                 V[e][k] = vr[i][j]; V[e + 1][k] = vi[i][j];
             }
-        smax[k] = sx; smin[k] = sn; s[k] = s32;
+        int32_t so = s32;
+        if (flags & SVD2O_BACKSCALE)
+            backscale_f(&sx, &sn, &so);
+        smax[k] = sx; smin[k] = sn; s[k] = so;
         if (flagged) flagged[k] = (uint8_t)flag;
     }
     return count;

@@ -57,6 +57,15 @@ def _declare(L):
         f = getattr(L, name)
         f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_uint32, P]
         f.restype = ctypes.c_int
+    for name in ("svd2_batch_s_rerun", "svd2_batch_c_rerun"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int, ctypes.c_uint32, P,
+                      ctypes.c_size_t, P]
+        f.restype = ctypes.c_int
+    L.svd2_rerun_workspace_bytes.argtypes = [ctypes.c_int64]
+    L.svd2_rerun_workspace_bytes.restype = ctypes.c_size_t
+    L.svd2_rerun_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    L.svd2_rerun_count.restype = ctypes.c_int
     L.svd2_set_launch.argtypes = [ctypes.c_int] * 5
     L.svd2_set_launch.restype = ctypes.c_int
     L.svd2_get_launch.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4
@@ -136,6 +145,45 @@ def svd2(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = N
            out.smin.data_ptr(), out.s.data_ptr(), BACKSCALE if backscale else 0, h)
     check(rc, "svd2_batch_" + kind)
     return out
+
+
+RERUN_TAU_LOG2 = -8
+
+
+def rerun_workspace(n: int, device="cuda") -> torch.Tensor:
+    """Device workspace for svd2_rerun (bytes as a uint8 tensor)."""
+    return torch.empty(int(lib().svd2_rerun_workspace_bytes(n)), dtype=torch.uint8, device=device)
+
+
+def svd2_rerun(A: torch.Tensor, *, tau_log2: int = RERUN_TAU_LOG2, backscale: bool = False,
+               out: Svd2Result | None = None, workspace: torch.Tensor | None = None,
+               stream: int | None = None) -> Svd2Result:
+    """FP32 form with FP64 re-run of the matrices with sigma'_min < 2^tau_log2 sigma'_max.
+    ``A`` is float32 of shape (4, n) or (8, n)."""
+    rows, n = A.shape
+    if A.dtype != torch.float32:
+        raise TypeError("svd2_rerun takes float32 input")
+    kind = _kind(rows, A.dtype)
+    a_ptrs = _rows(A, "A")
+    if out is None:
+        out = empty_result(rows, n, A.dtype, A.device)
+    if workspace is None:
+        workspace = rerun_workspace(n, A.device)
+    h = current_stream_handle(A.device) if stream is None else stream
+    f = getattr(lib(), f"svd2_batch_{kind}_rerun")
+    rc = f(n, ptr_array(a_ptrs), ptr_array(_rows(out.U, "U")), ptr_array(_rows(out.V, "V")),
+           out.smax.data_ptr(), out.smin.data_ptr(), out.s.data_ptr(), int(tau_log2),
+           BACKSCALE if backscale else 0, workspace.data_ptr(), workspace.numel(), h)
+    check(rc, f"svd2_batch_{kind}_rerun")
+    out.workspace = workspace
+    return out
+
+
+def rerun_count(workspace: torch.Tensor) -> int:
+    """Matrices re-run by the last completed call that used ``workspace``."""
+    c = ctypes.c_int64()
+    check(lib().svd2_rerun_count(workspace.data_ptr(), ctypes.byref(c)), "svd2_rerun_count")
+    return c.value
 
 
 def set_launch(kind: str, block: int, mpt: int, unroll: int, waves: int = 0):

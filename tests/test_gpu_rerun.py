@@ -1,0 +1,90 @@
+"""FP32 form with FP64 re-run against the oracle's re-run form (same flag
+decision in float, same double method, same rounding to float), bit for bit;
+the re-run count against the oracle's; and the stated error of the form
+against the double oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2005_07403_gb300 import inputs
+from paper_2005_07403_gb300 import svd2 as S
+from tests.helpers import bits_equal
+from tests.test_gpu_fwd import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+def run(A, tau, backscale=False):
+    Ad = torch.from_numpy(A).cuda()
+    r = S.svd2_rerun(Ad, tau_log2=tau, backscale=backscale)
+    torch.cuda.synchronize()
+    g = {k: getattr(r, k).cpu().numpy() for k in ("U", "V", "smax", "smin", "s")}
+    return g, S.rerun_count(r.workspace)
+
+
+@pytest.mark.parametrize("tau", [-8, -4, -20])
+def test_rerun_real_matches_oracle(tau):
+    A32, _ = inputs.real_fp32_illcond(2**17 + 11)
+    g, cnt = run(A32, tau)
+    o = oracle.svd2_rerun(A32, tau)
+    assert_same(g, o, f"s_rerun tau={tau}")
+    assert cnt == o["count"] > 0
+
+
+def test_rerun_complex_matches_oracle():
+    A = inputs.normal_batch(2**16 + 7, 8, 61, np.float32)
+    g, cnt = run(A, -6)
+    o = oracle.svd2_rerun(A, -6)
+    assert_same(g, o, "c_rerun")
+    assert cnt == o["count"] > 0
+
+
+def test_rerun_edge_and_backscale():
+    A = np.ascontiguousarray(np.concatenate([inputs.edge_real(np.float32),
+                                             inputs.random_bits_f32(4096, 4, 62)], axis=1))
+    for bs in (False, True):
+        g, cnt = run(A, -8, backscale=bs)
+        with np.errstate(all="ignore"):
+            o = oracle.svd2_rerun(A, -8, backscale=bs)
+        assert_same(g, o, f"rerun edge bs={bs}")
+        assert cnt == o["count"]
+
+
+def test_rerun_nothing_flagged_equals_plain_fp32():
+    A = inputs.normal_batch(10000, 4, 63, np.float32)
+    g, cnt = run(A, -100)
+    r = S.svd2(torch.from_numpy(A).cuda())
+    torch.cuda.synchronize()
+    assert cnt == 0
+    assert bits_equal(g["U"], r.U.cpu().numpy()) and bits_equal(g["smin"], r.smin.cpu().numpy())
+
+
+def test_rerun_stated_error_full_size_sampled():
+    """FP32 vs FP64 workload at n = 2^26: every sampled matrix's sigma'_max within
+    8 u of the double method, sigma'_min within 64 u for kept matrices
+    (u = 2^-24; measured on the oracle: <= 6.3 u and <= 47 u at tau = 2^-8)
+    and within 1 u + the double method's own error for re-run ones."""
+    A32, ill = inputs.real_fp32_illcond(2**26)
+    Ad = torch.from_numpy(A32).cuda()
+    r = S.svd2_rerun(Ad)
+    torch.cuda.synchronize()
+    cnt = S.rerun_count(r.workspace)
+    idx = np.sort(np.random.default_rng(5).choice(A32.shape[1], 1 << 16, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    sx = r.smax.index_select(0, it).cpu().numpy().astype(np.float64)
+    sn = r.smin.index_select(0, it).cpu().numpy().astype(np.float64)
+    s = r.s.index_select(0, it).cpu().numpy()
+    Asub = np.ascontiguousarray(A32[:, idx].astype(np.float64))
+    o64 = oracle.svd2(Asub, backscale=True)
+    u = 2.0**-24
+    bx = np.ldexp(sx, -s)
+    bn = np.ldexp(sn, -s)
+    ex = np.abs(bx - o64["smax"]) / o64["smax"]
+    assert ex.max() <= 8 * u
+    keep = sn >= 2.0**-8 * sx
+    en = np.abs(bn - o64["smin"]) / np.where(o64["smin"] > 0, o64["smin"], 1)
+    assert en[keep].max() <= 64 * u
+    assert en[~keep].max() <= 1.001 * u
+    frac = cnt / A32.shape[1]
+    assert 0.09 < frac < 0.12, frac
