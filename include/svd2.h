@@ -54,6 +54,7 @@ typedef struct CUstream_st *svd2_stream_t;
 #define SVD2_EINVAL (-1)
 #define SVD2_ECUDA (-2)
 #define SVD2_ENOMEM (-3)
+#define SVD2_ETOOBIG (-4)     /* n above the fixed capacity of an allocation-free entry point */
 
 #define SVD2_S_ZERO INT32_MAX      /* s of the all-zero matrix (Eq. 2: s = DBL_MAX) */
 #define SVD2_BACKSCALE 1u          /* store Sigma = 2^-s Sigma' and s = 0 (Fig. 1)  */
@@ -119,6 +120,29 @@ int svd2_batch_c_rerun(int64_t n, const float *const A[8], float *const U[8],
 /* Number of matrices re-run by the last call that used `workspace` (a device
  * pointer); synchronous: call it once that call has completed. */
 int svd2_rerun_count(const void *workspace, int64_t *count);
+
+/*
+ * svd2_batch_s_rerun without a workspace argument, for callers that cannot
+ * allocate device memory: an application whose device memory belongs to
+ * another allocator (a framework's caching pool, or a host program that gives
+ * this library only the input and output buffers), or code that must not call
+ * cudaMalloc once running (cudaMalloc may synchronise the device, which a
+ * latency-bound loop or a fixed start-up memory budget cannot accept).  The
+ * paper has no counterpart; it is a deployment variant of the re-run form.
+ * The scratch (counters and index list) is a fixed array of about 4 MiB in
+ * device memory, reserved on every device that loads the library until the
+ * process exits; n is limited to SVD2_NOALLOC_MAX_N matrices (larger n returns
+ * SVD2_ETOOBIG) -- split larger batches, or use svd2_batch_s_rerun.  The first
+ * call on a device (with that device current) looks up the array's address;
+ * make it before any stream capture.  The call allocates nothing.  All calls
+ * on one device share the array: calls whose GPU work may overlap (different
+ * streams with no ordering between them) race and must not be made.
+ * Arguments, results and other errors as svd2_batch_s_rerun.
+ */
+#define SVD2_NOALLOC_MAX_N (1 << 20)
+int svd2_batch_s_rerun_noalloc(int64_t n, const float *const A[4], float *const U[4],
+                               float *const V[4], float *smax, float *smin, int32_t *s,
+                               int tau_log2, uint32_t flags, svd2_stream_t stream);
 
 /*
  * Launch shape of the forward kernels.  op: 0 = d, 1 = z, 2 = s, 3 = c.

@@ -25,6 +25,8 @@ OK = 0
 EINVAL = -1
 ECUDA = -2
 ENOMEM = -3
+ETOOBIG = -4
+NOALLOC_MAX_N = 1 << 20
 S_ZERO = 2**31 - 1
 BACKSCALE = 1
 
@@ -62,6 +64,9 @@ def _declare(L):
         f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int, ctypes.c_uint32, P,
                       ctypes.c_size_t, P]
         f.restype = ctypes.c_int
+    L.svd2_batch_s_rerun_noalloc.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int,
+                                             ctypes.c_uint32, P]
+    L.svd2_batch_s_rerun_noalloc.restype = ctypes.c_int
     L.svd2_rerun_workspace_bytes.argtypes = [ctypes.c_int64]
     L.svd2_rerun_workspace_bytes.restype = ctypes.c_size_t
     L.svd2_rerun_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
