@@ -156,6 +156,18 @@ int svd2_batch_s_rerun_noalloc(int64_t n, const float *const A[4], float *const 
 int svd2_set_launch(int op, int block, int mpt, int unroll, int waves);
 int svd2_get_launch(int op, int *block, int *mpt, int *unroll, int *waves);
 
+/*
+ * Self-test of the library's double arithmetic.  The FP64 forms compute their
+ * divisions and square roots on the integer and FP32 pipes, exactly rounded
+ * to nearest even (on GB300 the hardware IEEE double division and square root
+ * take ~10 slots each of the narrow FP64 pipe).  For i < n this writes
+ * lib[i] = the library's result and hw[i] = the hardware instruction's
+ * (op 0: x[i] / y[i]; op 1: sqrt(x[i]); y unused for op 1).  All pointers are
+ * device arrays of n doubles.  The two must agree bit for bit.
+ */
+int svd2_arith_check(int op, int64_t n, const double *x, const double *y, double *lib,
+                     double *hw, svd2_stream_t stream);
+
 /* The cudaError_t of the last failed CUDA call made by this thread (0 if none). */
 int svd2_last_cuda_error(void);
 

@@ -1,0 +1,258 @@
+// Correctly rounded (round to nearest, ties to even) IEEE double division and
+// square root computed on the integer and FP32 pipes.
+//
+// On GB300 the FP64 pipe retires 2 lanes per clock per SM, and the hardware
+// IEEE double division and square root each take about ten of its slots, while
+// the integer and FP32 pipes are 32-64x wider.  The 2x2 SVD needs 10 (real) or
+// 24 (complex) divisions and 6 or 12 square roots per matrix, so these two
+// operations decide its speed.  The routines below return exactly the IEEE
+// result (the same bits as __ddiv_rn / __dsqrt_rn) for operands in their fast
+// domain -- normal operands and a normal result -- and defer to the hardware
+// instruction otherwise (zeros, subnormals, overflow, NaN), which keeps every
+// result bit-identical to IEEE arithmetic.
+//
+// Method (both operations): the 53-bit significand of the result is produced
+// as three digits of 24, 18 and 11 bits.  The first digit comes from the FP32
+// approximate reciprocal (square root: reciprocal square root) of the top 24
+// bits of the operand; each further digit is estimated in FP32 from the exact
+// residual, which is kept as a wrapping 64-bit integer (its true value is
+// small, so arithmetic modulo 2^64 gives it exactly).  A final exact residual
+// fixes the last unit, and its comparison with half a unit rounds to nearest,
+// ties to even (a square root is never exactly half way).  Conversions
+// between small integers (|x| < 2^22) and FP32 use the 1.5 * 2^23 bias, so the
+// only special-function-unit instruction is the approximate reciprocal.
+//
+// The error bounds that fix the digit sizes are stated inline; the routines
+// are tested against the hardware on random, structured and near-tie operands
+// on the host (with a perturbed seed) and on the GPU.
+#pragma once
+#include <cstdint>
+#include <cstring>
+
+#if defined(__CUDACC__)
+#define SFP_FN __host__ __device__ __forceinline__
+#else
+#define SFP_FN inline
+#endif
+
+namespace svd2 {
+namespace sfp {
+
+constexpr uint64_t kSign = 0x8000000000000000ull;
+constexpr uint64_t kAbs = 0x7fffffffffffffffull;
+constexpr uint64_t kFrac = 0x000fffffffffffffull;
+constexpr uint64_t kImpl = 0x0010000000000000ull;
+
+SFP_FN uint64_t dbits(double x) {
+#if defined(__CUDA_ARCH__)
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  return u;
+#endif
+}
+SFP_FN double dval(uint64_t u) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  std::memcpy(&x, &u, 8);
+  return x;
+#endif
+}
+SFP_FN uint32_t fbits(float x) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(x);
+#else
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  return u;
+#endif
+}
+SFP_FN float fval(uint32_t u) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(u);
+#else
+  float x;
+  std::memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+SFP_FN float fmul(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+SFP_FN float fadd(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+
+#if !defined(__CUDA_ARCH__)
+// Host stand-ins for the approximate reciprocal instructions, used only to
+// test the integer logic on the CPU.  They return the float nearest to the
+// exact value moved by up to +-SFP_HOST_PERTURB_ULPS units in the last place
+// (a deterministic function of the argument), wider than the hardware's error.
+#ifndef SFP_HOST_PERTURB_ULPS
+#define SFP_HOST_PERTURB_ULPS 2
+#endif
+inline float host_perturb(float r, float x) {
+  uint32_t h = fbits(x) * 2654435761u;
+  int k = (int)((h >> 24) % (2u * SFP_HOST_PERTURB_ULPS + 1u)) - SFP_HOST_PERTURB_ULPS;
+  uint32_t b = fbits(r);
+  return fval((uint32_t)((int32_t)b + k));
+}
+#endif
+
+// ~1/x for x in [2^22, 2^24] (an FP32 approximation good to ~2^-22 relative).
+SFP_FN float rcp_approx(float x) {
+#if defined(__CUDA_ARCH__)
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  return host_perturb((float)(1.0 / (double)x), x);
+#endif
+}
+// ~1/sqrt(x) for x in [2^22, 2^24].
+SFP_FN float rsqrt_approx(float x) {
+#if defined(__CUDA_ARCH__)
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  double s = 1.0;
+  {
+    // a correctly rounded double square root, then the reciprocal
+    double v = (double)x;
+    s = 1.0 / __builtin_sqrt(v);
+  }
+  return host_perturb((float)s, x);
+#endif
+}
+
+// x as a float, exactly, for |x| < 2^22 (1.5 * 2^23 bias).
+SFP_FN float i2f_small(int32_t x) { return fadd(fval(0x4B400000u + (uint32_t)x), -12582912.0f); }
+// the nearest integer to y, for |y| < 2^22.
+SFP_FN int32_t f2i_small(float y) { return (int32_t)(fbits(fadd(y, 12582912.0f)) - 0x4B400000u); }
+// an integer v in [2^22, 2^24) as a float, exactly.
+SFP_FN float u24_to_f(uint32_t v) {
+  return v >= 0x800000u ? fval(0x4B000000u | (v & 0x7FFFFFu))
+                        : fval(0x4A800000u | ((v << 1) & 0x7FFFFFu));
+}
+// the integer nearest to a float y in about [2^23 - 8, 2^24 + 8], clamped to [2^23, 2^24 - 1].
+SFP_FN uint32_t f_to_u24_clamped(float y) {
+  const float c = y < 8388608.0f ? 8388608.0f : (y > 16777215.0f ? 16777215.0f : y);
+  return (fbits(c) & 0x7FFFFFu) | 0x800000u;
+}
+
+SFP_FN double hw_div(double a, double b) {
+#if defined(__CUDA_ARCH__)
+  return __ddiv_rn(a, b);
+#else
+  return a / b;
+#endif
+}
+SFP_FN double hw_sqrt(double a) {
+#if defined(__CUDA_ARCH__)
+  return __dsqrt_rn(a);
+#else
+  return __builtin_sqrt(a);
+#endif
+}
+
+// Wrapping 64-bit product of a signed and an unsigned operand (the true
+// values of the residuals below are small; only their low 64 bits are formed).
+SFP_FN uint64_t mulw(int64_t a, uint64_t b) { return (uint64_t)a * b; }
+
+// RN(a / b).
+SFP_FN double div_rn(double a, double b) {
+  const uint64_t ua = dbits(a), ub = dbits(b);
+  const uint64_t sgn = (ua ^ ub) & kSign;
+  const uint32_t ea = (uint32_t)(ua >> 52) & 0x7ffu, eb = (uint32_t)(ub >> 52) & 0x7ffu;
+  const int e0 = (int)ea - (int)eb + 1023;
+  const bool b_normal = eb - 1u < 2046u;
+  if ((ua & kAbs) == 0 && b_normal) return dval(sgn);          // +-0 / normal
+  // fast domain: a, b normal and the quotient's exponent in [1, 2045] whichever
+  // way the significand quotient falls, so the result is normal
+  if (!(ea - 1u < 2046u && b_normal && (unsigned)(e0 - 2) < 2044u)) return hw_div(a, b);
+  const uint64_t ma = (ua & kFrac) | kImpl, mb = (ub & kFrac) | kImpl;
+  const bool lt = ma < mb;
+  const uint64_t A = lt ? ma << 1 : ma;     // A in [mb, 2 mb): A/mb in [1, 2)
+  const int e = e0 - (lt ? 1 : 0);
+  // Q = floor(A 2^52 / mb) in [2^52, 2^53), built as q0 2^29 + q1 2^11 + q2.
+  const float fb = fval(0x4B000000u | ((uint32_t)(mb >> 29) & 0x7FFFFFu));   // mb >> 29, exact
+  const float fa = fval(0x4B000000u | ((uint32_t)(ma >> 29) & 0x7FFFFFu));   // ma >> 29, exact
+  const float r = rcp_approx(fb);
+  // relative error of r fa / (ma / mb) is at most 2^-23 (fa) + 2^-23 (fb) +
+  // 2^-22 (r) + 2^-23 (two roundings) < 2^-20.6
+  // digit 0 (24 bits): q0 ~ A 2^23 / mb, within 10.5
+  const uint32_t q0 = f_to_u24_clamped(fmul(fmul(fa, r), lt ? 16777216.0f : 8388608.0f));
+  int64_t R = (int64_t)((A << 23) - (uint64_t)q0 * mb);                // |R| <= 10.5 mb < 2^56.4
+  // digit 1 (18 bits): q1 ~ R 2^18 / mb ~ (R >> 35) 2^53 / mb ~ (R >> 35) r 2^24,
+  // |q1| < 2^21.4; error <= 2 (truncation) + 1.3 (relative) + 0.5 (rounding)
+  const int32_t q1 = f2i_small(fmul(fmul(i2f_small((int32_t)(R >> 35)), r), 16777216.0f));
+  R = (int64_t)(((uint64_t)R << 18) - mulw(q1, mb));                    // |R| <= 3.8 mb < 2^55
+  // digit 2 (11 bits): q2 ~ R 2^11 / mb ~ (R >> 34) r 2^16, |q2| < 2^13; error < 0.51
+  const int32_t q2 = f2i_small(fmul(fmul(i2f_small((int32_t)(R >> 34)), r), 65536.0f));
+  R = (int64_t)(((uint64_t)R << 11) - mulw(q2, mb));                    // |R| < 0.51 mb
+  uint64_t Q = ((uint64_t)q0 << 29) + ((uint64_t)(int64_t)q1 << 11) + (uint64_t)(int64_t)q2;
+  // exact floor and remainder: R = A 2^52 - Q mb in [0, mb)
+  if (R < 0) { Q -= 1; R += (int64_t)mb; }
+  if (R < 0) { Q -= 1; R += (int64_t)mb; }
+  if (R >= (int64_t)mb) { Q += 1; R -= (int64_t)mb; }
+  // round to nearest, ties to even
+  const uint64_t twoR = (uint64_t)R << 1;
+  Q += (twoR > mb || (twoR == mb && (Q & 1))) ? 1 : 0;
+  // Q in [2^52, 2^53]; Q = 2^53 carries into the exponent field
+  return dval(sgn | (((uint64_t)(e - 1) << 52) + Q));
+}
+
+// RN(sqrt(x)).
+SFP_FN double sqrt_rn(double x) {
+  const uint64_t ux = dbits(x);
+  const uint32_t ex = (uint32_t)(ux >> 52);        // includes the sign bit
+  if (!(ex - 1u < 2046u)) return hw_sqrt(x);       // +-0, subnormal, negative, inf, NaN
+  const uint64_t mx = (ux & kFrac) | kImpl;
+  const int E = (int)ex - 1023;
+  const int odd = E & 1;
+  const uint64_t X = mx << odd;                    // X in [2^52, 2^54), E - odd even
+  const int er = ((E - odd) >> 1) + 1023;          // result exponent, always normal
+  // S = floor(sqrt(X 2^52)) in [2^52, 2^53), built as s0 2^29 + d1 2^11 + d2.
+  const float fx = u24_to_f((uint32_t)(X >> 30));  // X >> 30 in [2^22, 2^24), exact
+  const float y = rsqrt_approx(fx);                // ~fx^-1/2
+  // digit 0 (24 bits): s0 ~ sqrt(fx) 2^12 ~ S / 2^29, within 8.5
+  const uint32_t s0 = f_to_u24_clamped(fmul(fmul(fx, y), 4096.0f));
+  // R1 = (X 2^52 - (s0 2^29)^2) / 2^52 exactly; |R1| < 2^34.1
+  const int64_t R1 = (int64_t)(X - (((uint64_t)s0 * s0) << 6));
+  // digit 1 (18 bits): the Newton step S - s0 2^29 ~ R1 2^52 / (2 s0 2^29), in units of
+  // 2^11: d1 ~ R1 / (2 s0) 2^12 ~ R1 y / 2 (1/s0 ~ y 2^-12); |d1| < 2^21.1;
+  // error <= 2 (truncation) + 2.3 (y for 1/s0) + 1.1 (Newton's square term) + 0.5
+  const int32_t d1 = f2i_small(fmul(fmul(i2f_small((int32_t)(R1 >> 13)), y), 4096.0f));
+  const uint64_t S2 = ((uint64_t)s0 << 29) + ((uint64_t)(int64_t)d1 << 11);
+  // R2 = (X 2^52 - S2^2) / 2^22 = R1 2^30 - s0 d1 2^19 - d1^2; |R2| < 2^45.6
+  const int64_t R2 = (int64_t)(((uint64_t)R1 << 30) - ((uint64_t)((int64_t)s0 * d1) << 19) -
+                               (uint64_t)((int64_t)d1 * d1));
+  // digit 2 (11 bits): d2 ~ R2 2^22 / (2 S2) ~ (R2 >> 24) y 2^4, |d2| < 2^13.6; error < 0.53
+  const int32_t d2 = f2i_small(fmul(fmul(i2f_small((int32_t)(R2 >> 24)), y), 16.0f));
+  uint64_t S = S2 + (uint64_t)(int64_t)d2;
+  // R = X 2^52 - S^2 = R2 2^22 - 2 S2 d2 - d2^2, |R| < 2^55
+  int64_t R = (int64_t)(((uint64_t)R2 << 22) - (mulw(d2, S2) << 1) -
+                        (uint64_t)((int64_t)d2 * d2));
+  // exact floor: R = X 2^52 - S^2 in [0, 2S]
+  if (R < 0) { R += (int64_t)(2 * S - 1); S -= 1; }
+  if (R < 0) { R += (int64_t)(2 * S - 1); S -= 1; }
+  if (R > (int64_t)(2 * S)) { R -= (int64_t)(2 * S + 1); S += 1; }
+  // round to nearest (a square root is never half way): up iff R > S
+  S += (R > (int64_t)S) ? 1 : 0;
+  return dval(((uint64_t)(er - 1) << 52) + S);
+}
+
+}  // namespace sfp
+}  // namespace svd2

@@ -71,6 +71,8 @@ def _declare(L):
     L.svd2_rerun_workspace_bytes.restype = ctypes.c_size_t
     L.svd2_rerun_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     L.svd2_rerun_count.restype = ctypes.c_int
+    L.svd2_arith_check.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, P, P]
+    L.svd2_arith_check.restype = ctypes.c_int
     L.svd2_set_launch.argtypes = [ctypes.c_int] * 5
     L.svd2_set_launch.restype = ctypes.c_int
     L.svd2_get_launch.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4
@@ -189,6 +191,19 @@ def rerun_count(workspace: torch.Tensor) -> int:
     c = ctypes.c_int64()
     check(lib().svd2_rerun_count(workspace.data_ptr(), ctypes.byref(c)), "svd2_rerun_count")
     return c.value
+
+
+def arith_check(op: str, x: torch.Tensor, y: torch.Tensor | None = None):
+    """The library's double division ("div") or square root ("sqrt") next to the
+    hardware instruction, on float64 CUDA tensors; returns (lib, hw)."""
+    lib_out = torch.empty_like(x)
+    hw_out = torch.empty_like(x)
+    code = {"div": 0, "sqrt": 1}[op]
+    rc = lib().svd2_arith_check(code, x.numel(), x.data_ptr(),
+                                None if y is None else y.data_ptr(), lib_out.data_ptr(),
+                                hw_out.data_ptr(), current_stream_handle(x.device))
+    check(rc, "svd2_arith_check")
+    return lib_out, hw_out
 
 
 def set_launch(kind: str, block: int, mpt: int, unroll: int, waves: int = 0):

@@ -1,0 +1,95 @@
+// Host check of the integer-pipe IEEE division and square root
+// (paper_2005_07403_gb300/csrc/svd2_softfp.cuh) against the CPU's correctly
+// rounded hardware division and square root, bit for bit.  The header's host
+// build replaces the FP32 approximate reciprocals by the nearest float moved
+// by up to +-2 units in the last place, wider than the GPU instructions'
+// error.  Usage: softfp_host_check <count per class> <seed>; prints the
+// number of checked cases and mismatches, exits 1 on any mismatch.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "svd2_softfp.cuh"
+
+using svd2::sfp::dbits;
+using svd2::sfp::dval;
+
+static uint64_t sm64(uint64_t &s) {  // SplitMix64
+  uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+static long long checked = 0, bad = 0;
+
+static void chk_div(double a, double b) {
+  const double r = svd2::sfp::div_rn(a, b), h = a / b;
+  ++checked;
+  if (dbits(r) != dbits(h) && !(std::isnan(r) && std::isnan(h))) {
+    if (bad < 10) std::printf("div mismatch a=%a b=%a soft=%a hw=%a\n", a, b, r, h);
+    ++bad;
+  }
+}
+static void chk_sqrt(double x) {
+  const double r = svd2::sfp::sqrt_rn(x), h = std::sqrt(x);
+  ++checked;
+  if (dbits(r) != dbits(h) && !(std::isnan(r) && std::isnan(h))) {
+    if (bad < 10) std::printf("sqrt mismatch x=%a soft=%a hw=%a\n", x, r, h);
+    ++bad;
+  }
+}
+
+// a double with the given biased exponent and mantissa bits
+static double mk(uint64_t sign, uint64_t bexp, uint64_t frac) {
+  return dval((sign << 63) | ((bexp & 0x7ff) << 52) | (frac & 0xfffffffffffffull));
+}
+
+int main(int argc, char **argv) {
+  const long long n = argc > 1 ? std::atoll(argv[1]) : 1000000;
+  uint64_t s = argc > 2 ? std::strtoull(argv[2], nullptr, 10) : 1;
+  const uint64_t specials[] = {0, 1, 2, 3, 0xfffffffffffffull, 0xffffffffffffeull,
+                               0x8000000000000ull, 0x7ffffffffffffull, 0x0000000000001ull,
+                               0xaaaaaaaaaaaaaull, 0x5555555555555ull, 0xfffff00000000ull,
+                               0x00000fffffffful, 0x1000000000000ull};
+  for (long long i = 0; i < n; ++i) {
+    // uniform random bit patterns (any class: normal, subnormal, zero, inf, NaN)
+    chk_div(dval(sm64(s)), dval(sm64(s)));
+    chk_sqrt(dval(sm64(s)));
+    // random mantissas, exponents near each other (the method's typical use)
+    const uint64_t ea = 1023 + (sm64(s) % 64) - 32, eb = 1023 + (sm64(s) % 64) - 32;
+    chk_div(mk(sm64(s) & 1, ea, sm64(s)), mk(sm64(s) & 1, eb, sm64(s)));
+    chk_sqrt(mk(0, ea, sm64(s)));
+    // structured mantissas (all ones, single bits, runs)
+    const uint64_t fa = specials[sm64(s) % 14] ^ ((sm64(s) % 4 == 0) ? (1ull << (sm64(s) % 52)) : 0);
+    const uint64_t fb = specials[sm64(s) % 14] ^ ((sm64(s) % 4 == 0) ? (1ull << (sm64(s) % 52)) : 0);
+    chk_div(mk(0, ea, fa), mk(0, eb, fb));
+    chk_sqrt(mk(0, ea, fa));
+    chk_sqrt(mk(0, ea + 1, fb));
+    // exponent extremes: results near overflow and underflow, subnormal operands
+    const uint64_t e1 = 1 + sm64(s) % 2046, e2 = 1 + sm64(s) % 2046;
+    chk_div(mk(0, e1, sm64(s)), mk(1, e2, sm64(s)));
+    chk_div(mk(0, 0, sm64(s)), mk(0, e2, sm64(s)));
+    chk_sqrt(mk(0, 0, sm64(s)));
+    // exact squares and neighbours: sqrt results near a representable value
+    const uint64_t t = (sm64(s) >> 38) | (1ull << 25);     // 26-bit integer
+    const double sq = (double)t * (double)t;               // exact
+    chk_sqrt(sq);
+    chk_sqrt(std::nextafter(sq, 0.0));
+    chk_sqrt(std::nextafter(sq, 1e300));
+    // quotients near integers: a = b * k (+-1 ulp)
+    const double bb = mk(0, 1023, sm64(s));
+    const double kk = (double)(1 + sm64(s) % 1000);
+    const double aa = bb * kk;
+    chk_div(aa, bb);
+    chk_div(std::nextafter(aa, 0.0), bb);
+    chk_div(std::nextafter(aa, 1e300), bb);
+    // ratios within an ulp of 1, and b with short mantissas
+    chk_div(std::nextafter(bb, 0.0), bb);
+    chk_div(mk(0, ea, sm64(s)), mk(0, eb, (sm64(s) % 4096) << 40));
+  }
+  std::printf("checked %lld mismatches %lld\n", checked, bad);
+  return bad ? 1 : 0;
+}

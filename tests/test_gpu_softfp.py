@@ -1,0 +1,69 @@
+"""The library's double division and square root (integer/FP32 pipes) against
+the GPU's own IEEE instructions, bit for bit, through svd2_arith_check."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2005_07403_gb300 import svd2 as S
+
+pytestmark = pytest.mark.gpu
+
+N = 1 << 24
+
+
+def _bits(n, seed):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    hi = torch.randint(0, 2**32, (n,), generator=g, device="cuda", dtype=torch.int64)
+    lo = torch.randint(0, 2**32, (n,), generator=g, device="cuda", dtype=torch.int64)
+    return (hi << 32) | lo
+
+
+def _with_exponent(bits, lo, hi, seed):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    e = torch.randint(lo, hi, bits.shape, generator=g, device="cuda", dtype=torch.int64)
+    frac = bits & ((1 << 52) - 1)
+    sign = (bits >> 63) & 1
+    return ((sign << 63) | (e << 52) | frac).view(torch.float64)
+
+
+def _same(a, b):
+    a = a.view(torch.int64)
+    b = b.view(torch.int64)
+    nan = torch.isnan(a.view(torch.float64)) & torch.isnan(b.view(torch.float64))
+    return bool(torch.all((a == b) | nan).item())
+
+
+@pytest.mark.parametrize("cls", ["anybits", "near", "wide", "ulp1"])
+def test_division_matches_hardware(cls):
+    if cls == "anybits":
+        x = _bits(N, 1).view(torch.float64)
+        y = _bits(N, 2).view(torch.float64)
+    elif cls == "near":            # exponents near each other: the method's use
+        x = _with_exponent(_bits(N, 3), 1000, 1046, 4)
+        y = _with_exponent(_bits(N, 5), 1000, 1046, 6)
+    elif cls == "wide":            # the whole normal range: over/underflowing quotients
+        x = _with_exponent(_bits(N, 7), 1, 2047, 8)
+        y = _with_exponent(_bits(N, 9), 1, 2047, 10)
+    else:                          # quotients within an ulp of 1 and of small integers
+        y = _with_exponent(_bits(N, 11), 1023, 1024, 12)
+        k = torch.randint(1, 1000, (N,), device="cuda", dtype=torch.float64)
+        x = torch.nextafter(y * k, torch.full_like(y, float("inf")))
+    lib, hw = S.arith_check("div", x, y)
+    torch.cuda.synchronize()
+    assert _same(lib, hw), cls
+
+
+@pytest.mark.parametrize("cls", ["anybits", "normal", "squares"])
+def test_sqrt_matches_hardware(cls):
+    if cls == "anybits":
+        x = _bits(N, 21).view(torch.float64)
+    elif cls == "normal":
+        x = _with_exponent(_bits(N, 22), 1, 2047, 23).abs()
+    else:                          # exact squares and their neighbours
+        t = torch.randint(2**25, 2**26, (N // 3,), device="cuda", dtype=torch.int64).double()
+        sq = t * t
+        x = torch.cat([sq, torch.nextafter(sq, torch.zeros_like(sq)),
+                       torch.nextafter(sq, torch.full_like(sq, float("inf")))])
+    lib, hw = S.arith_check("sqrt", x)
+    torch.cuda.synchronize()
+    assert _same(lib, hw), cls
