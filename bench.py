@@ -36,13 +36,32 @@ sys.path.insert(0, ROOT)
 METRIC = "2x2 SVDs/sec and achieved HBM GB/s vs peak, FP64 vs FP32 at stated error"
 FALLBACK_HBM_GBS = 6800.0
 
-# Algorithmic bytes per matrix: one read of A, one write of U, V, Sigma', s (int32).
+# Workloads.  Algorithmic bytes per matrix: one read of A, one write of U, V,
+# Sigma' and s (int32).  The default is the complex128 batch; the others are
+# the FP32-vs-FP64 batch of n = 2^26 (90% N(0,1), 10% ill-conditioned, rounded
+# to FP32; the FP64 form runs on its exact widening) in each form.
 WORKLOADS = {
-    "complex128": dict(rows=8, dtype="float64", n=2**24, bytes_per=64 + 64 + 64 + 8 + 8 + 4,
-                       kind="z",
+    "complex128": dict(rows=8, n=2**24, bytes_per=64 + 128 + 16 + 4, kind="z", form="plain",
+                       dtype="f64",
                        desc="complex128 n=2^24, parts U[-1,1]*2^e, e in [-500,500] per matrix, "
                             "1% rank-deficient"),
+    "real-fp64": dict(rows=4, n=2**26, bytes_per=32 + 64 + 16 + 4, kind="d", form="plain",
+                      dtype="f64",
+                      desc="real FP64 n=2^26 (FP32-vs-FP64 batch widened exactly)"),
+    "real-fp32": dict(rows=4, n=2**26, bytes_per=16 + 32 + 8 + 4, kind="s", form="plain",
+                      dtype="f32", desc="real FP32 n=2^26 (FP32-vs-FP64 batch), no re-run"),
+    "real-fp32-rerun": dict(rows=4, n=2**26, bytes_per=16 + 32 + 8 + 4, kind="s", form="rerun",
+                            dtype="f32",
+                            desc="real FP32 n=2^26 with FP64 re-run below tau = 2^-8"),
 }
+
+
+def make_input(name, n, rank):
+    from paper_2005_07403_gb300 import inputs
+    if name == "complex128":
+        return inputs.complex_scaled(n, seed=inputs.SEED_CFG2 + rank)
+    A32, _ = inputs.real_fp32_illcond(n, seed=inputs.SEED_CFG3 + rank)
+    return A32.astype(np.float64) if name == "real-fp64" else A32
 
 
 def parse():
@@ -56,6 +75,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n", type=int, default=0,
                    help="override the batch size (small cases for profiling only)")
+    p.add_argument("--no-compare", action="store_true",
+                   help="skip the FP32-vs-FP64 comparison block")
     return p.parse_args()
 
 
@@ -151,22 +172,27 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_2005_07403_gb300 import inputs
     W = WORKLOADS[args.workload]
     sample = 2**21
-    A = inputs.complex_scaled(sample)
-    oracle.svd2(A[:, :1024].copy())
+    A = make_input(args.workload, sample, 0)
+    if W["form"] == "rerun":
+        def run(a):
+            return oracle.svd2_rerun(a, -8)
+    else:
+        def run(a):
+            return oracle.svd2(a)
+    run(np.ascontiguousarray(A[:, :1024]))
     for _ in range(args.warmup):
-        oracle.svd2(A)
+        run(A)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.svd2(A)
+        run(A)
     el = time.perf_counter() - t0
     value = args.steps * sample / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
             "config": {"workload": W["desc"], "sample_per_step": sample},
             "cpu_baseline": {"value": value, "unit": "matrices/s", "kind": "oracle",
                              "cores": oracle.max_threads(),
@@ -176,9 +202,107 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _caller(S, W, Ad, out, workspace):
+    if W["form"] == "rerun":
+        return lambda: S.svd2_rerun(Ad, out=out, workspace=workspace)
+    return lambda: S.svd2(Ad, out=out)
+
+
+def time_steps(torch, call, steps, warmup, stream):
+    for _ in range(max(warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def compare_fp32_fp64(torch, S, steps, warmup, stream, n=2**26):
+    """FP32 form (with FP64 re-run) against the FP64 form on the same inputs:
+    matrices/s of each and the FP32 form's error against the FP64 form (which
+    reproduces the FP64 method bit for bit), on the whole batch."""
+    from paper_2005_07403_gb300 import inputs
+    A32, _ = inputs.real_fp32_illcond(n)
+    A32d = torch.from_numpy(A32).cuda()
+    A64d = A32d.double()
+    del A32
+    o64 = S.empty_result(4, n, torch.float64, A64d.device)
+    o32 = S.empty_result(4, n, torch.float32, A32d.device)
+    ws = S.rerun_workspace(n)
+    ms64 = time_steps(torch, lambda: S.svd2(A64d, out=o64), steps, warmup, stream)
+    ms32r = time_steps(torch, lambda: S.svd2_rerun(A32d, out=o32, workspace=ws), steps, warmup,
+                       stream)
+    rerun = S.rerun_count(ws)
+    ms32 = time_steps(torch, lambda: S.svd2(A32d, out=o32), steps, warmup, stream)
+    S.svd2_rerun(A32d, out=o32, workspace=ws)
+    torch.cuda.synchronize()
+    u = 2.0**-24
+    sx64 = torch.ldexp(o64.smax, -o64.s.double())
+    sn64 = torch.ldexp(o64.smin, -o64.s.double())
+    sx32 = torch.ldexp(o32.smax.double(), -o32.s.double())
+    sn32 = torch.ldexp(o32.smin.double(), -o32.s.double())
+    nz = o64.smax > 0
+    ex = ((sx32 - sx64).abs() / sx64)[nz]
+    keep = (o32.smin >= 2.0**S.RERUN_TAU_LOG2 * o32.smax) & nz & (sn64 > 0)
+    en = ((sn32 - sn64).abs() / sn64)
+    out = {"n": n, "tau_log2": S.RERUN_TAU_LOG2,
+           "fp64": {"matrices_per_s": n / (ms64 / 1e3), "ms": ms64},
+           "fp32_rerun": {"matrices_per_s": n / (ms32r / 1e3), "ms": ms32r,
+                          "rerun_fraction": rerun / n},
+           "fp32_plain": {"matrices_per_s": n / (ms32 / 1e3), "ms": ms32},
+           "fp32_rerun_error_vs_fp64_u": {
+               "smax_max": float(ex.max() / u),
+               "smin_max_kept": float(en[keep].max() / u),
+               "smin_max_rerun": float(en[~keep & nz & (sn64 > 0)].max() / u),
+               "u": "2^-24"}}
+    del A32d, A64d, o64, o32, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_multi(torch, S, stream, replays=20):
+    """The Kogbetliantz batching workload: 2048 batches with lengths log-uniform
+    in [16, 2^20], real FP64 / complex128 at random, N(0,1) entries (drawn on
+    the device); the autotuner picks the launch shape, the persistent launch is
+    captured in a CUDA graph and each replay is timed; the median is reported."""
+    from paper_2005_07403_gb300 import inputs
+    lens, cplx = inputs.kog_batches()
+    dev = [inputs.normal_batch_device(int(n), 8 if c else 4, 5000 + i)
+           for i, (n, c) in enumerate(zip(lens, cplx))]
+    total = int(lens.sum())
+    mb = S.MultiBatch(dev)
+    best = mb.autotune(reps=3)
+    g = mb.graph()
+    for _ in range(3):
+        g.launch()
+    torch.cuda.synchronize()
+    times = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(replays):
+        e0.record(stream)
+        g.launch(stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    g.close()
+    med = float(np.median(times))
+    nbytes = int(sum(n * (212 if c else 116) for n, c in zip(lens, cplx)))
+    out = {"batches": int(len(lens)), "matrices": total, "complex_fraction": float(cplx.mean()),
+           "tuned_shape": best, "graph_replays": replays, "median_ms": med,
+           "matrices_per_s": total / (med / 1e3), "algorithmic_GBps": nbytes / (med / 1e3) / 1e9}
+    del dev, mb
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
-    from paper_2005_07403_gb300 import inputs
     from paper_2005_07403_gb300 import svd2 as S
 
     rank, world, local = dist_env()
@@ -189,9 +313,11 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     W = WORKLOADS[args.workload]
     n = args.n or W["n"]
-    A = inputs.complex_scaled(n, seed=inputs.SEED_CFG2 + rank)
+    A = make_input(args.workload, n, rank)
     Ad = torch.from_numpy(A).cuda()
     out = S.empty_result(W["rows"], n, Ad.dtype, Ad.device)
+    workspace = S.rerun_workspace(n) if W["form"] == "rerun" else None
+    call = _caller(S, W, Ad, out, workspace)
     S.lib()
     stream = torch.cuda.current_stream()
 
@@ -202,7 +328,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(max(args.warmup, 3)):
-        S.svd2(Ad, out=out)
+        call()
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -211,7 +337,7 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        S.svd2(Ad, out=out)
+        call()
     e1.record(stream)
     barrier()
     ms = e0.elapsed_time(e1)
@@ -222,6 +348,7 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     ms_per_step = ms_max / args.steps
     value = world * n * args.steps / (ms_max / 1e3)
+    launches_per_step = 2 if W["form"] == "rerun" else 1
 
     # end to end through the public API with host buffers: H2D of A, the call,
     # D2H of every output, each step
@@ -238,7 +365,7 @@ def run_ours(args):
                 barrier()
                 e0.record(stream)
             Ad.copy_(Ah, non_blocking=True)
-            S.svd2(Ad, out=out)
+            call()
             for th, td in zip(outs_h, (out.U, out.V, out.smax, out.smin, out.s)):
                 th.copy_(td, non_blocking=True)
         e1.record(stream)
@@ -249,6 +376,7 @@ def run_ours(args):
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
         e2e = {"value": world * n * ke / (float(et.item()) / 1e3), "unit": "matrices/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        del Ah, outs_h
 
     peak, peak_src = measured_peaks()
     bytes_launch = W["bytes_per"] * n
@@ -258,11 +386,20 @@ def run_ours(args):
                 "note": f"peak {peak_src}; algorithmic {W['bytes_per']} B/matrix x {n} per launch"}
     line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": W["desc"], "n_per_gpu": n, "l2": "inputs larger than L2 (1 GiB)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": W["dtype"], "data": "synthetic",
+            "config": {"workload": W["desc"], "n_per_gpu": n,
+                       "l2": "inputs larger than L2 (>= 1 GiB per step)",
                        "launch": S.get_launch(W["kind"])},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk}
+            "roofline": roofline, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_compare and args.workload == "complex128" \
+            and not args.n:
+        del Ad, out
+        torch.cuda.empty_cache()
+        line["fp32_vs_fp64"] = compare_fp32_fp64(torch, S, max(3, min(args.steps, 10)),
+                                                 args.warmup, stream)
+        line["multi_batch"] = bench_multi(torch, S, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, W["rows"])
     if dist is not None:

@@ -145,6 +145,72 @@ int svd2_batch_s_rerun_noalloc(int64_t n, const float *const A[4], float *const 
                                int tau_log2, uint32_t flags, svd2_stream_t stream);
 
 /*
+ * Many batches in one persistent launch (the batches of one or more parallel
+ * Kogbetliantz steps, Sec. 1), real FP64 and complex FP64 mixed.  Each batch is
+ * described as for svd2_batch_d / svd2_batch_z; the batches are cut into tiles
+ * of block * mpt * unroll matrices and a persistent grid walks the tiles in a
+ * fixed round-robin order (no atomics, no scratch, deterministic; the results
+ * equal those of one svd2_batch_d / svd2_batch_z call per batch).
+ *
+ * svd2_multi_plan_bytes(nbatch): device bytes of a plan for nbatch batches.
+ * svd2_multi_prepare: writes the plan for this launch shape (block a multiple
+ *   of 32 in 32..512, mpt in {1, 2}, unroll in {1, 2}) to the caller-owned
+ *   device buffer `plan` (16-byte aligned) with a synchronous copy, and returns
+ *   the tile count in *total_tiles (may be NULL).  descs is a host array.
+ * svd2_multi_run: one persistent launch over the plan, asynchronous on
+ *   `stream`; block, mpt and unroll must be those of the plan (otherwise the
+ *   launch does nothing); grid 0 = SMs x resident blocks per SM.
+ * svd2_multi_graph_create: the same launch captured into an executable CUDA
+ *   graph (*graph_exec), replayed with svd2_graph_launch and freed with
+ *   svd2_graph_destroy.  The plan and the batch arrays must stay allocated
+ *   while the graph is used; their contents may change between replays.
+ */
+#define SVD2_KIND_D 0
+#define SVD2_KIND_Z 1
+typedef struct svd2_batch_desc {
+  int32_t kind;        /* SVD2_KIND_D or SVD2_KIND_Z */
+  uint32_t flags;      /* 0 or SVD2_BACKSCALE */
+  int64_t n;           /* matrices in this batch */
+  const void *a[8];    /* element arrays of A (4 used when real), record order */
+  void *u[8];
+  void *v[8];
+  void *smax;
+  void *smin;
+  int32_t *s;
+} svd2_batch_desc;
+size_t svd2_multi_plan_bytes(int32_t nbatch);
+int svd2_multi_prepare(const svd2_batch_desc *descs, int32_t nbatch, int block, int mpt,
+                       int unroll, void *plan, size_t plan_bytes, int64_t *total_tiles);
+int svd2_multi_run(const void *plan, int block, int mpt, int unroll, int grid,
+                   svd2_stream_t stream);
+int svd2_multi_graph_create(const void *plan, int block, int mpt, int unroll, int grid,
+                            void **graph_exec);
+int svd2_graph_launch(void *graph_exec, svd2_stream_t stream);
+int svd2_graph_destroy(void *graph_exec);
+
+/*
+ * Autotuner.  svd2_autotune_fwd times the forward kernel of op (0 = d, 1 = z,
+ * 2 = s, 3 = c) on the caller's batch (arguments as for svd2_batch_*) for
+ * every block in {64, 128, 256, 512}, mpt in {1, 2, 4}, unroll in {1, 2} and
+ * waves in {0, 4}, `reps` timed launches each after one warm-up launch, sets
+ * the fastest as the op's launch shape and returns it with its time per launch
+ * (ms).  svd2_multi_autotune does the same for the persistent multi-batch
+ * launch (block in {64, 128, 256, 512}, mpt and unroll in {1, 2}), leaving
+ * `plan` prepared for the winning shape.  Both synchronise the stream, write
+ * the outputs (as a normal call would) and allocate nothing on the device.
+ */
+typedef struct svd2_tune_result {
+  int block, mpt, unroll, waves;
+  float ms;
+} svd2_tune_result;
+int svd2_autotune_fwd(int op, int64_t n, const void *const *A, void *const *U, void *const *V,
+                      void *smax, void *smin, int32_t *s, int reps, svd2_tune_result *best,
+                      svd2_stream_t stream);
+int svd2_multi_autotune(const svd2_batch_desc *descs, int32_t nbatch, void *plan,
+                        size_t plan_bytes, int reps, svd2_tune_result *best,
+                        svd2_stream_t stream);
+
+/*
  * Launch shape of the forward kernels.  op: 0 = d, 1 = z, 2 = s, 3 = c.
  * block: threads per block (a multiple of 32, 32..512); mpt: matrices per
  * thread per load (1, 2 or 4); unroll: load groups in flight per thread (1 or

@@ -252,3 +252,13 @@ def edge_real(dtype=np.float64) -> np.ndarray:
     A = np.array(cases, dtype=np.float64).T
     with np.errstate(over="ignore", under="ignore"):
         return np.ascontiguousarray(A.astype(dtype))
+
+
+def normal_batch_device(n: int, rows: int, seed: int, device="cuda", dtype=None):
+    """i.i.d. N(0,1) entries of shape (rows, n), drawn on the GPU by torch's
+    seeded Philox generator (for workloads too large to draw on the host, such
+    as the 2048-batch Kogbetliantz sequence)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.randn((rows, n), generator=g, device=device, dtype=dtype or torch.float64)

@@ -40,6 +40,27 @@ class Svd2Error(RuntimeError):
     pass
 
 
+KIND_D = 0
+KIND_Z = 1
+
+
+class BatchDesc(ctypes.Structure):
+    """svd2_batch_desc of include/svd2.h."""
+    _fields_ = [("kind", ctypes.c_int32), ("flags", ctypes.c_uint32), ("n", ctypes.c_int64),
+                ("a", ctypes.c_void_p * 8), ("u", ctypes.c_void_p * 8), ("v", ctypes.c_void_p * 8),
+                ("smax", ctypes.c_void_p), ("smin", ctypes.c_void_p), ("s", ctypes.c_void_p)]
+
+
+class TuneResult(ctypes.Structure):
+    """svd2_tune_result of include/svd2.h."""
+    _fields_ = [("block", ctypes.c_int), ("mpt", ctypes.c_int), ("unroll", ctypes.c_int),
+                ("waves", ctypes.c_int), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"block": self.block, "mpt": self.mpt, "unroll": self.unroll,
+                "waves": self.waves, "ms": self.ms}
+
+
 def lib():
     """Load (building first if sources changed) the CUDA library."""
     global _lib
@@ -71,6 +92,27 @@ def _declare(L):
     L.svd2_rerun_workspace_bytes.restype = ctypes.c_size_t
     L.svd2_rerun_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     L.svd2_rerun_count.restype = ctypes.c_int
+    L.svd2_multi_plan_bytes.argtypes = [ctypes.c_int32]
+    L.svd2_multi_plan_bytes.restype = ctypes.c_size_t
+    L.svd2_multi_prepare.argtypes = [ctypes.POINTER(BatchDesc), ctypes.c_int32, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_int64)]
+    L.svd2_multi_prepare.restype = ctypes.c_int
+    L.svd2_multi_run.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    L.svd2_multi_run.restype = ctypes.c_int
+    L.svd2_multi_graph_create.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    L.svd2_multi_graph_create.restype = ctypes.c_int
+    L.svd2_graph_launch.argtypes = [P, P]
+    L.svd2_graph_launch.restype = ctypes.c_int
+    L.svd2_graph_destroy.argtypes = [P]
+    L.svd2_graph_destroy.restype = ctypes.c_int
+    L.svd2_autotune_fwd.argtypes = [ctypes.c_int, ctypes.c_int64, PP, PP, PP, P, P, P,
+                                    ctypes.c_int, ctypes.POINTER(TuneResult), P]
+    L.svd2_autotune_fwd.restype = ctypes.c_int
+    L.svd2_multi_autotune.argtypes = [ctypes.POINTER(BatchDesc), ctypes.c_int32, P,
+                                      ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(TuneResult), P]
+    L.svd2_multi_autotune.restype = ctypes.c_int
     L.svd2_arith_check.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, P, P]
     L.svd2_arith_check.restype = ctypes.c_int
     L.svd2_set_launch.argtypes = [ctypes.c_int] * 5
@@ -204,6 +246,108 @@ def arith_check(op: str, x: torch.Tensor, y: torch.Tensor | None = None):
                                 hw_out.data_ptr(), current_stream_handle(x.device))
     check(rc, "svd2_arith_check")
     return lib_out, hw_out
+
+
+def autotune_fwd(A: torch.Tensor, out: Svd2Result | None = None, reps: int = 5) -> dict:
+    """Time every launch shape of A's form on A (svd2_autotune_fwd) and keep the
+    fastest as that form's launch shape.  Returns the winning shape."""
+    rows, n = A.shape
+    kind = _kind(rows, A.dtype)
+    if out is None:
+        out = empty_result(rows, n, A.dtype, A.device)
+    res = TuneResult()
+    rc = lib().svd2_autotune_fwd(OPS[kind], n, ptr_array(_rows(A, "A")),
+                                 ptr_array(_rows(out.U, "U")), ptr_array(_rows(out.V, "V")),
+                                 out.smax.data_ptr(), out.smin.data_ptr(), out.s.data_ptr(),
+                                 reps, ctypes.byref(res), current_stream_handle(A.device))
+    check(rc, "svd2_autotune_fwd")
+    return res.as_dict()
+
+
+class MultiBatch:
+    """Several FP64 batches (real (4, n_i) and complex (8, n_i) float64 CUDA
+    tensors) decomposed by one persistent launch (svd2_multi_*).  Outputs are
+    allocated here, one Svd2Result per batch; the input tensors may be
+    overwritten between runs (a Kogbetliantz step updates them in place)."""
+
+    def __init__(self, batches, block: int = 256, mpt: int = 1, unroll: int = 1,
+                 backscale: bool = False):
+        self.inputs = list(batches)
+        self.outputs = []
+        descs = (BatchDesc * max(1, len(self.inputs)))()
+        for i, A in enumerate(self.inputs):
+            rows, n = A.shape
+            if A.dtype != torch.float64 or rows not in (4, 8):
+                raise ValueError("MultiBatch takes float64 (4, n) or (8, n) batches")
+            out = empty_result(rows, n, A.dtype, A.device)
+            self.outputs.append(out)
+            d = descs[i]
+            d.kind = KIND_Z if rows == 8 else KIND_D
+            d.flags = BACKSCALE if backscale else 0
+            d.n = n
+            for e, p in enumerate(_rows(A, "A")):
+                d.a[e] = p
+            for e, p in enumerate(_rows(out.U, "U")):
+                d.u[e] = p
+            for e, p in enumerate(_rows(out.V, "V")):
+                d.v[e] = p
+            d.smax, d.smin, d.s = out.smax.data_ptr(), out.smin.data_ptr(), out.s.data_ptr()
+        self.descs = descs
+        self.nbatch = len(self.inputs)
+        dev = self.inputs[0].device if self.inputs else torch.device("cuda")
+        self.plan = torch.empty(int(lib().svd2_multi_plan_bytes(self.nbatch)), dtype=torch.uint8,
+                                device=dev)
+        self.prepare(block, mpt, unroll)
+
+    def prepare(self, block, mpt, unroll):
+        tiles = ctypes.c_int64()
+        check(lib().svd2_multi_prepare(self.descs, self.nbatch, block, mpt, unroll,
+                                       self.plan.data_ptr(), self.plan.numel(),
+                                       ctypes.byref(tiles)), "svd2_multi_prepare")
+        self.shape = (block, mpt, unroll)
+        self.tiles = tiles.value
+
+    def run(self, stream: int | None = None, grid: int = 0):
+        h = current_stream_handle(self.plan.device) if stream is None else stream
+        check(lib().svd2_multi_run(self.plan.data_ptr(), *self.shape, grid, h), "svd2_multi_run")
+
+    def autotune(self, reps: int = 5) -> dict:
+        res = TuneResult()
+        check(lib().svd2_multi_autotune(self.descs, self.nbatch, self.plan.data_ptr(),
+                                        self.plan.numel(), reps, ctypes.byref(res),
+                                        current_stream_handle(self.plan.device)),
+              "svd2_multi_autotune")
+        self.shape = (res.block, res.mpt, res.unroll)
+        return res.as_dict()
+
+    def graph(self) -> "Graph":
+        h = ctypes.c_void_p()
+        check(lib().svd2_multi_graph_create(self.plan.data_ptr(), *self.shape, 0, ctypes.byref(h)),
+              "svd2_multi_graph_create")
+        return Graph(h, self)
+
+
+class Graph:
+    """An executable CUDA graph of one persistent multi-batch launch."""
+
+    def __init__(self, handle, owner):
+        self.handle = handle
+        self.owner = owner   # keeps the plan and the batch tensors alive
+
+    def launch(self, stream: int | None = None):
+        h = current_stream_handle(self.owner.plan.device) if stream is None else stream
+        check(lib().svd2_graph_launch(self.handle, h), "svd2_graph_launch")
+
+    def close(self):
+        if self.handle:
+            check(lib().svd2_graph_destroy(self.handle), "svd2_graph_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def set_launch(kind: str, block: int, mpt: int, unroll: int, waves: int = 0):
