@@ -145,6 +145,30 @@ int svd2_batch_s_rerun_noalloc(int64_t n, const float *const A[4], float *const 
                                int tau_log2, uint32_t flags, svd2_stream_t stream);
 
 /*
+ * Backward (adjoint) of the real 2x2 SVD, FP64 and FP32.  The paper defines
+ * no backward; this is the differentiation form built on its forward.  For
+ * A = U diag(s1, s2) V^T and a loss with gradients gU, gV (element order
+ * u11, u21, u12, u22) and g1, g2, it writes
+ *   gA = U M V^T,  M = [[g1, p - q], [-p - q, g2]],  J = U^T gU,  K = V^T gV,
+ *   a = J12 - J21,  b = K12 - K21,  p = (a-b)/(2(s1+s2)),  q = (a+b)/(2(s1-s2)),
+ * with 1/(s1 - s2) replaced by g / (s1 (g^2 + rel_delta^2)), g = (s1 - s2)/s1,
+ * which equals it for g >> rel_delta and stays bounded as the singular values
+ * meet (rel_delta >= 0; 0 disables the safeguard).  s1, s2 are the singular
+ * values themselves (back-scaled: a forward call with SVD2_BACKSCALE).  U, V,
+ * s1, s2 as produced by svd2_batch_d / svd2_batch_s.  gU, gV may be NULL (and
+ * their entries, g1, g2) to mean zero gradients.  Device arrays of n values,
+ * asynchronous on stream; errors as above.
+ */
+int svd2_bwd_d(int64_t n, const double *const U[4], const double *const V[4],
+               const double *s1, const double *s2, const double *const gU[4],
+               const double *const gV[4], const double *g1, const double *g2,
+               double *const gA[4], double rel_delta, svd2_stream_t stream);
+int svd2_bwd_s(int64_t n, const float *const U[4], const float *const V[4],
+               const float *s1, const float *s2, const float *const gU[4],
+               const float *const gV[4], const float *g1, const float *g2,
+               float *const gA[4], float rel_delta, svd2_stream_t stream);
+
+/*
  * Many batches in one persistent launch (the batches of one or more parallel
  * Kogbetliantz steps, Sec. 1), real FP64 and complex FP64 mixed.  Each batch is
  * described as for svd2_batch_d / svd2_batch_z; the batches are cut into tiles

@@ -1,0 +1,135 @@
+// Backward (adjoint) of the real batched 2x2 SVD: svd2_bwd_d / svd2_bwd_s.
+//
+// For A = U diag(s1, s2) V^T (s1 >= s2 >= 0, U and V orthogonal) and a loss
+// with gradients gU, gV (element order u11, u21, u12, u22) and g1, g2, the
+// gradient with respect to A is, with J = U^T gU, K = V^T gV, a = J12 - J21,
+// b = K12 - K21:
+//   gA = U M V^T,  M = [[g1, p - q], [-p - q, g2]],
+//   p = (a - b) / (2 (s1 + s2)),  q = (a + b) / (2 (s1 - s2)).
+// (The standard square-SVD adjoint: dP = U^T dA V has diagonal d(s) and
+// off-diagonal Omega_U Sigma + Sigma Omega_V^T with antisymmetric Omega's, which
+// for order two solve in closed form.)  The paper defines no backward; this is
+// the differentiation form built on its forward.
+//
+// Near-equal singular values: 1/(s1 - s2) is replaced, with the relative gap
+// g = (s1 - s2)/s1, by g / (s1 (g^2 + rel_delta^2)) -- equal to 1/(s1 - s2)
+// for g >> rel_delta and going to 0 as g -> 0 -- so the rotation part of the
+// gradient stays bounded when the singular vectors are ill-determined.
+// s1 + s2 = 0 (A = 0) zeroes both rotation terms.  NULL upstream gradients
+// count as zero.  Every operation is a correctly rounded IEEE operation in the
+// order written, as in the oracle's adjoint.
+#include "svd2_common.cuh"
+#include "svd2_math.cuh"
+
+namespace svd2 {
+
+template <typename T>
+struct BwdArgs {
+  const T *u[4];
+  const T *v[4];
+  const T *s1;
+  const T *s2;
+  const T *gu[4];   // entries may be NULL (zero)
+  const T *gv[4];
+  const T *g1;
+  const T *g2;
+  T *ga[4];
+  T dl;
+  int64_t n;
+};
+
+template <typename T>
+__device__ __forceinline__ T ld0(const T *p, int64_t k) {
+  return p ? __ldcs(p + k) : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs<T> p) {
+  using F = fp<T>;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride) {
+    const T u11 = __ldcs(p.u[0] + k), u21 = __ldcs(p.u[1] + k);
+    const T u12 = __ldcs(p.u[2] + k), u22 = __ldcs(p.u[3] + k);
+    const T v11 = __ldcs(p.v[0] + k), v21 = __ldcs(p.v[1] + k);
+    const T v12 = __ldcs(p.v[2] + k), v22 = __ldcs(p.v[3] + k);
+    const T s1 = __ldcs(p.s1 + k), s2 = __ldcs(p.s2 + k);
+    const T gu11 = ld0(p.gu[0], k), gu21 = ld0(p.gu[1], k);
+    const T gu12 = ld0(p.gu[2], k), gu22 = ld0(p.gu[3], k);
+    const T gv11 = ld0(p.gv[0], k), gv21 = ld0(p.gv[1], k);
+    const T gv12 = ld0(p.gv[2], k), gv22 = ld0(p.gv[3], k);
+    // J12 = (U^T gU)_12, J21 = (U^T gU)_21, likewise K for V
+    const T J12 = F::add(F::mul(u11, gu12), F::mul(u21, gu22));
+    const T J21 = F::add(F::mul(u12, gu11), F::mul(u22, gu21));
+    const T K12 = F::add(F::mul(v11, gv12), F::mul(v21, gv22));
+    const T K21 = F::add(F::mul(v12, gv11), F::mul(v22, gv21));
+    const T a = F::sub(J12, J21), b = F::sub(K12, K21);
+    const T sum = F::add(s1, s2);
+    const T inv_sum = sum > T(0) ? F::div(T(1), sum) : T(0);
+    T inv_gap = T(0);
+    if (s1 > T(0)) {
+      const T g = F::div(F::sub(s1, s2), s1);
+      inv_gap = F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
+    }
+    const T pp = F::mul(F::mul(T(0.5), F::sub(a, b)), inv_sum);
+    const T qq = F::mul(F::mul(T(0.5), F::add(a, b)), inv_gap);
+    const T m11 = ld0(p.g1, k), m22 = ld0(p.g2, k);
+    const T m12 = F::sub(pp, qq), m21 = F::sub(b_neg(pp), qq);
+    // W = U M, gA = W V^T
+    const T w11 = F::add(F::mul(u11, m11), F::mul(u12, m21));
+    const T w12 = F::add(F::mul(u11, m12), F::mul(u12, m22));
+    const T w21 = F::add(F::mul(u21, m11), F::mul(u22, m21));
+    const T w22 = F::add(F::mul(u21, m12), F::mul(u22, m22));
+    __stcs(p.ga[0] + k, F::add(F::mul(w11, v11), F::mul(w12, v12)));
+    __stcs(p.ga[1] + k, F::add(F::mul(w21, v11), F::mul(w22, v12)));
+    __stcs(p.ga[2] + k, F::add(F::mul(w11, v21), F::mul(w12, v22)));
+    __stcs(p.ga[3] + k, F::add(F::mul(w21, v21), F::mul(w22, v22)));
+  }
+}
+
+template <typename T>
+static int launch_bwd(int64_t n, const T *const *U, const T *const *V, const T *s1, const T *s2,
+                      const T *const *gU, const T *const *gV, const T *g1, const T *g2,
+                      T *const *gA, T rel_delta, cudaStream_t stream) {
+  if (n < 0 || !(rel_delta >= T(0))) return SVD2_EINVAL;
+  if (n == 0) return SVD2_OK;
+  if (!U || !V || !gA || !s1 || !s2) return SVD2_EINVAL;
+  BwdArgs<T> p{};
+  for (int e = 0; e < 4; ++e) {
+    if (!U[e] || !V[e] || !gA[e]) return SVD2_EINVAL;
+    p.u[e] = U[e];
+    p.v[e] = V[e];
+    p.gu[e] = gU ? gU[e] : nullptr;
+    p.gv[e] = gV ? gV[e] : nullptr;
+    p.ga[e] = gA[e];
+  }
+  p.s1 = s1;
+  p.s2 = s2;
+  p.g1 = g1;
+  p.g2 = g2;
+  p.dl = rel_delta;
+  p.n = n;
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  bwd_kernel<T><<<grid, 256, 0, stream>>>(p);
+  SVD2_CUDA_TRY(cudaGetLastError());
+  return SVD2_OK;
+}
+
+}  // namespace svd2
+
+using namespace svd2;
+
+extern "C" int svd2_bwd_d(int64_t n, const double *const U[4], const double *const V[4],
+                          const double *s1, const double *s2, const double *const gU[4],
+                          const double *const gV[4], const double *g1, const double *g2,
+                          double *const gA[4], double rel_delta, svd2_stream_t stream) {
+  return launch_bwd<double>(n, U, V, s1, s2, gU, gV, g1, g2, gA, rel_delta, (cudaStream_t)stream);
+}
+
+extern "C" int svd2_bwd_s(int64_t n, const float *const U[4], const float *const V[4],
+                          const float *s1, const float *s2, const float *const gU[4],
+                          const float *const gV[4], const float *g1, const float *g2,
+                          float *const gA[4], float rel_delta, svd2_stream_t stream) {
+  return launch_bwd<float>(n, U, V, s1, s2, gU, gV, g1, g2, gA, rel_delta, (cudaStream_t)stream);
+}

@@ -113,6 +113,10 @@ def _declare(L):
     L.svd2_multi_autotune.argtypes = [ctypes.POINTER(BatchDesc), ctypes.c_int32, P,
                                       ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(TuneResult), P]
     L.svd2_multi_autotune.restype = ctypes.c_int
+    L.svd2_bwd_d.argtypes = [ctypes.c_int64, PP, PP, P, P, PP, PP, P, P, PP, ctypes.c_double, P]
+    L.svd2_bwd_d.restype = ctypes.c_int
+    L.svd2_bwd_s.argtypes = [ctypes.c_int64, PP, PP, P, P, PP, PP, P, P, PP, ctypes.c_float, P]
+    L.svd2_bwd_s.restype = ctypes.c_int
     L.svd2_arith_check.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, P, P]
     L.svd2_arith_check.restype = ctypes.c_int
     L.svd2_set_launch.argtypes = [ctypes.c_int] * 5
@@ -246,6 +250,40 @@ def arith_check(op: str, x: torch.Tensor, y: torch.Tensor | None = None):
                                 hw_out.data_ptr(), current_stream_handle(x.device))
     check(rc, "svd2_arith_check")
     return lib_out, hw_out
+
+
+def default_rel_delta(dtype) -> float:
+    """Relative singular-value gap below which the adjoint's rotation term is
+    damped: 64 units of roundoff of the dtype."""
+    return 64 * torch.finfo(dtype).eps
+
+
+def _opt_rows(t, n, what):
+    if t is None:
+        return None
+    return ptr_array(_rows(t, what))
+
+
+def svd2_bwd(U, V, s1, s2, gU=None, gV=None, g1=None, g2=None, rel_delta=None,
+             out: torch.Tensor | None = None, stream: int | None = None) -> torch.Tensor:
+    """Adjoint of the real 2x2 SVD (svd2_bwd_d / svd2_bwd_s): gA (4, n) from U, V
+    (4, n), the singular values s1, s2 (n,) and the upstream gradients (None =
+    zero)."""
+    rows, n = U.shape
+    if rows != 4 or U.dtype not in (torch.float64, torch.float32):
+        raise ValueError("svd2_bwd takes real (4, n) float64/float32 factors")
+    if rel_delta is None:
+        rel_delta = default_rel_delta(U.dtype)
+    if out is None:
+        out = torch.empty_like(U)
+    f = lib().svd2_bwd_d if U.dtype == torch.float64 else lib().svd2_bwd_s
+    h = current_stream_handle(U.device) if stream is None else stream
+    p = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    rc = f(n, ptr_array(_rows(U, "U")), ptr_array(_rows(V, "V")), s1.data_ptr(), s2.data_ptr(),
+           _opt_rows(gU, n, "gU"), _opt_rows(gV, n, "gV"), p(g1), p(g2),
+           ptr_array(_rows(out, "gA")), float(rel_delta), h)
+    check(rc, "svd2_bwd")
+    return out
 
 
 def autotune_fwd(A: torch.Tensor, out: Svd2Result | None = None, reps: int = 5) -> dict:
