@@ -81,8 +81,8 @@ def parse():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
-            int(os.environ.get("LOCAL_RANK", 0)))
+    from paper_2005_07403_gb300 import distributed as D
+    return D.env()
 
 
 def measured_peaks():
@@ -301,6 +301,34 @@ def bench_multi(torch, S, stream, replays=20):
     return out
 
 
+def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
+    """The differentiation workload: A = R(t1) diag(s1, s2) R(t2)^T, 10% with
+    relative gaps in [1e-12, 1e-6], N(0,1) upstream gradients; one step is the
+    forward kernel (with back-scaling) plus the adjoint kernel, FP64 and FP32."""
+    from paper_2005_07403_gb300 import inputs
+    g = inputs.grad_batch(n)
+    out = {"n": n}
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        A = torch.from_numpy(g["A"]).to("cuda", dt)
+        gU = torch.from_numpy(g["gU"]).to("cuda", dt)
+        gV = torch.from_numpy(g["gV"]).to("cuda", dt)
+        gS = torch.from_numpy(g["gS"]).to("cuda", dt)
+        r = S.empty_result(4, n, dt, A.device)
+        gA = torch.empty_like(A)
+
+        def step():
+            S.svd2(A, backscale=True, out=r)
+            S.svd2_bwd(r.U, r.V, r.smax, r.smin, gU, gV, gS[0], gS[1], out=gA)
+
+        ms = time_steps(torch, step, steps, warmup, stream)
+        msf = time_steps(torch, lambda: S.svd2(A, backscale=True, out=r), steps, warmup, stream)
+        out[name] = {"fwd_bwd_matrices_per_s": n / (ms / 1e3), "fwd_bwd_ms": ms,
+                     "bwd_ms": ms - msf}
+        del A, gU, gV, gS, r, gA
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2005_07403_gb300 import svd2 as S
@@ -400,6 +428,7 @@ def run_ours(args):
         line["fp32_vs_fp64"] = compare_fp32_fp64(torch, S, max(3, min(args.steps, 10)),
                                                  args.warmup, stream)
         line["multi_batch"] = bench_multi(torch, S, stream)
+        line["differentiation"] = bench_grad(torch, S, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, W["rows"])
     if dist is not None:
