@@ -235,6 +235,24 @@ int svd2_multi_autotune(const svd2_batch_desc *descs, int32_t nbatch, void *plan
                         svd2_stream_t stream);
 
 /*
+ * The forward forms (op 0 = d, 1 = z, 2 = s, 3 = c) on a batch held in HOST
+ * memory: A, U, V are host arrays of host element pointers, smax, smin, s host
+ * arrays, in the layout above.  The batch is cut into chunks of `chunk`
+ * matrices (0 = 2^21; rounded up to a multiple of 64) that are copied to the
+ * device, decomposed and copied back through a double-buffered three-stream
+ * pipeline, so the copies in both directions overlap the kernels.  The call is
+ * asynchronous on `stream`: the stream waits for the last chunk's outputs, and
+ * the host arrays must stay valid (and unmodified) until then.  Host memory
+ * should be pinned for the copies to overlap.  The device staging buffers
+ * (two chunks of inputs and outputs) and the pipeline's streams are created by
+ * the first call on a device and kept until the process exits; calls are
+ * serialised within the process.  Errors as above.
+ */
+int svd2_batch_host(int op, int64_t n, const void *const *A, void *const *U, void *const *V,
+                    void *smax, void *smin, int32_t *s, uint32_t flags, int64_t chunk,
+                    svd2_stream_t stream);
+
+/*
  * Launch shape of the forward kernels.  op: 0 = d, 1 = z, 2 = s, 3 = c.
  * block: threads per block (a multiple of 32, 32..512); mpt: matrices per
  * thread per load (1, 2 or 4); unroll: load groups in flight per thread (1 or

@@ -91,8 +91,13 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
   store_vec<int32_t, M>(p.s + k0, so);
 }
 
+// Minimum resident 512-thread blocks per SM the compiler must allow for: the
+// complex FP64 kernel is bound by arithmetic latency and runs best at 64
+// registers (32 warps per SM at 256 threads); the others may use up to 128.
+template <typename T, bool CPLX> constexpr int kMinBlocks = (sizeof(T) == 8 && CPLX) ? 2 : 1;
+
 template <typename T, bool CPLX, int M, int UNR, bool FLAG = false>
-__global__ void __launch_bounds__(512) fwd_kernel(const FwdArgs<T, CPLX ? 8 : 4> p) {
+__global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>) fwd_kernel(const FwdArgs<T, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
   const int64_t ngroups = p.n / M;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

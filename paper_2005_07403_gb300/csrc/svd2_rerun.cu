@@ -88,7 +88,11 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
   auto *count = total + 1;
   auto *list = reinterpret_cast<uint32_t *>(ws + kListOffset);
   SVD2_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(unsigned long long), stream));
-  const int grid2 = 2 * sm_count();
+  // pass 2 covers a device-resident count with a grid-stride loop: one
+  // resident wave of blocks, enough warps to hide its scattered accesses
+  int resident = 0;
+  SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, rerun_kernel<CPLX>, 256, 0));
+  const int grid2 = sm_count() * (resident > 0 ? resident : 1);
   for (int64_t base = 0; base < n; base += kChunk) {
     const int64_t m = (n - base < kChunk) ? (n - base) : kChunk;
     const float *a[NA];

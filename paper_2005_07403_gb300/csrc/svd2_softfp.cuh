@@ -152,6 +152,7 @@ SFP_FN uint32_t f_to_u24_clamped(float y) {
   return (fbits(c) & 0x7FFFFFu) | 0x800000u;
 }
 
+// The hardware instructions, for the operands outside the fast domain.
 SFP_FN double hw_div(double a, double b) {
 #if defined(__CUDA_ARCH__)
   return __ddiv_rn(a, b);

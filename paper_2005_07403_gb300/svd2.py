@@ -117,6 +117,9 @@ def _declare(L):
     L.svd2_bwd_d.restype = ctypes.c_int
     L.svd2_bwd_s.argtypes = [ctypes.c_int64, PP, PP, P, P, PP, PP, P, P, PP, ctypes.c_float, P]
     L.svd2_bwd_s.restype = ctypes.c_int
+    L.svd2_batch_host.argtypes = [ctypes.c_int, ctypes.c_int64, PP, PP, PP, P, P, P,
+                                  ctypes.c_uint32, ctypes.c_int64, P]
+    L.svd2_batch_host.restype = ctypes.c_int
     L.svd2_arith_check.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, P, P]
     L.svd2_arith_check.restype = ctypes.c_int
     L.svd2_set_launch.argtypes = [ctypes.c_int] * 5
@@ -197,6 +200,40 @@ def svd2(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = N
     rc = f(n, ptr_array(a_ptrs), ptr_array(u_ptrs), ptr_array(v_ptrs), out.smax.data_ptr(),
            out.smin.data_ptr(), out.s.data_ptr(), BACKSCALE if backscale else 0, h)
     check(rc, "svd2_batch_" + kind)
+    return out
+
+
+def _host_rows(t: torch.Tensor, what: str):
+    if t.is_cuda or t.dim() != 2 or t.shape[0] not in (4, 8):
+        raise ValueError(f"{what} must be a host tensor of shape (4, n) or (8, n)")
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError(f"{what}: each row must be contiguous")
+    return [t[i].data_ptr() for i in range(t.shape[0])]
+
+
+def empty_host_result(rows: int, n: int, dtype, pin: bool = True) -> Svd2Result:
+    mk = (lambda *a, **k: torch.empty(*a, **k).pin_memory()) if pin else torch.empty
+    return Svd2Result(U=mk((rows, n), dtype=dtype), V=mk((rows, n), dtype=dtype),
+                      smax=mk(n, dtype=dtype), smin=mk(n, dtype=dtype), s=mk(n, dtype=torch.int32))
+
+
+def svd2_host(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = None,
+              chunk: int = 0, device=None, stream: int | None = None) -> Svd2Result:
+    """Forward form on a batch in host memory (svd2_batch_host): A is a CPU
+    tensor (pinned for overlap) of shape (4, n) or (8, n); outputs are host
+    tensors.  Asynchronous on the device's current stream (or ``stream``):
+    synchronise before reading the outputs."""
+    rows, n = A.shape
+    kind = _kind(rows, A.dtype)
+    if out is None:
+        out = empty_host_result(rows, n, A.dtype)
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    h = current_stream_handle(dev) if stream is None else stream
+    rc = lib().svd2_batch_host(OPS[kind], n, ptr_array(_host_rows(A, "A")),
+                               ptr_array(_host_rows(out.U, "U")), ptr_array(_host_rows(out.V, "V")),
+                               out.smax.data_ptr(), out.smin.data_ptr(), out.s.data_ptr(),
+                               BACKSCALE if backscale else 0, int(chunk), h)
+    check(rc, "svd2_batch_host")
     return out
 
 
