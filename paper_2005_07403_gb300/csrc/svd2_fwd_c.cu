@@ -8,6 +8,6 @@ extern "C" int svd2_batch_c(int64_t n, const float *const A[8], float *const U[8
                             float *const V[8], float *smax, float *smin, int32_t *s,
                             uint32_t flags, svd2_stream_t stream) {
   FwdArgs<float, 8> p{};
-  return launch_fwd<float, true, false>(kOpC, n, A, U, V, smax, smin, s, flags, (cudaStream_t)stream,
+  return launch_fwd<float, true>(kOpC, n, A, U, V, smax, smin, s, flags, (cudaStream_t)stream,
                                     p);
 }

@@ -8,6 +8,6 @@ extern "C" int svd2_batch_d(int64_t n, const double *const A[4], double *const U
                             double *const V[4], double *smax, double *smin, int32_t *s,
                             uint32_t flags, svd2_stream_t stream) {
   FwdArgs<double, 4> p{};
-  return launch_fwd<double, false, false>(kOpD, n, A, U, V, smax, smin, s, flags, (cudaStream_t)stream,
+  return launch_fwd<double, false>(kOpD, n, A, U, V, smax, smin, s, flags, (cudaStream_t)stream,
                                     p);
 }

@@ -1,5 +1,6 @@
-// Forward kernel template shared by the plain forms (svd2_fwd.cu) and the
-// FP32 form with FP64 re-run (svd2_rerun.cu).
+// Forward kernel template of the plain forms (svd2_fwd_{d,z,s,c}.cu); its
+// argument block, vector helpers and back-scaling are shared with the FP32 form
+// with FP64 re-run (svd2_rerun.cu).
 //
 // One thread owns `mpt` consecutive matrices of the split layout (Sec. 3) per
 // load group and keeps everything in registers from the load of A to the
@@ -24,27 +25,10 @@ struct FwdArgs {
   int32_t *s;
   int64_t n;
   uint32_t flags;
-  // FP32 form with FP64 re-run only: flag sigma'_min < tau sigma'_max and
-  // append the matrix index to list (count = its length).
+  // FP32 form with FP64 re-run only: re-run threshold and re-run counter.
   T tau;
-  uint32_t *list;
   unsigned long long *count;
 };
-
-// Warp-aggregated append of `idx` (for the lanes with f set) to list: one
-// atomic per warp and call.  All active lanes of the warp take part.
-__device__ __forceinline__ void append_flagged(bool f, uint32_t idx, uint32_t *list,
-                                               unsigned long long *count) {
-  const unsigned mask = __activemask();
-  const unsigned b = __ballot_sync(mask, f);
-  if (b == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(b) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(b));
-  base = __shfl_sync(mask, base, leader);
-  if (f) list[base + __popc(b & ((1u << lane) - 1u))] = idx;
-}
 
 // Optional back-scaling of Fig. 1: Sigma = 2^-s Sigma' (correctly rounded,
 // may overflow or underflow), then s = 0.
@@ -57,7 +41,7 @@ __device__ __forceinline__ void backscale(T &smax, T &smin, int32_t &s) {
   s = 0;
 }
 
-template <typename T, bool CPLX, int M, bool FLAG>
+template <typename T, bool CPLX, int M>
 __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p, int64_t k0,
                                               const T (&in)[CPLX ? 8 : 4][M]) {
   constexpr int NA = CPLX ? 8 : 4;
@@ -73,8 +57,6 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
       svd2_cplx<T>(a, u, v, sx[m], sn[m], so[m], piv);
     else
       svd2_real<T>(a, u, v, sx[m], sn[m], so[m], piv);
-    if constexpr (FLAG)
-      append_flagged(sn[m] < fp<T>::mul(p.tau, sx[m]), (uint32_t)(k0 + m), p.list, p.count);
     if (p.flags & SVD2_BACKSCALE) backscale(sx[m], sn[m], so[m]);
 #pragma unroll
     for (int e = 0; e < NA; ++e) {
@@ -96,7 +78,7 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
 // registers (32 warps per SM at 256 threads); the others may use up to 128.
 template <typename T, bool CPLX> constexpr int kMinBlocks = (sizeof(T) == 8 && CPLX) ? 2 : 1;
 
-template <typename T, bool CPLX, int M, int UNR, bool FLAG = false>
+template <typename T, bool CPLX, int M, int UNR>
 __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>) fwd_kernel(const FwdArgs<T, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
   const int64_t ngroups = p.n / M;
@@ -115,7 +97,7 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>) fwd_kernel(const Fwd
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
       const int64_t g = g0 + r * stride;
-      if (g < ngroups) process_group<T, CPLX, M, FLAG>(p, g * M, in[r]);
+      if (g < ngroups) process_group<T, CPLX, M>(p, g * M, in[r]);
     }
   }
   // the n mod M tail, one matrix per thread
@@ -124,25 +106,25 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>) fwd_kernel(const Fwd
     T in1[NA][1];
 #pragma unroll
     for (int e = 0; e < NA; ++e) in1[e][0] = p.a[e][k];
-    process_group<T, CPLX, 1, FLAG>(p, k, in1);
+    process_group<T, CPLX, 1>(p, k, in1);
   }
 }
 
-template <typename T, bool CPLX, bool FLAG>
+template <typename T, bool CPLX>
 using FwdKernel = void (*)(const FwdArgs<T, CPLX ? 8 : 4>);
 
-template <typename T, bool CPLX, bool FLAG>
-inline FwdKernel<T, CPLX, FLAG> pick_kernel(int mpt, int unroll) {
+template <typename T, bool CPLX>
+inline FwdKernel<T, CPLX> pick_kernel(int mpt, int unroll) {
 #define SVD2_PICK(M_, U_) \
-  if (mpt == M_ && unroll == U_) return fwd_kernel<T, CPLX, M_, U_, FLAG>;
+  if (mpt == M_ && unroll == U_) return fwd_kernel<T, CPLX, M_, U_>;
   SVD2_PICK(1, 1) SVD2_PICK(1, 2) SVD2_PICK(2, 1) SVD2_PICK(2, 2) SVD2_PICK(4, 1) SVD2_PICK(4, 2)
 #undef SVD2_PICK
   return nullptr;
 }
 
-// Validate the arguments, fill p (except the re-run fields) and launch the
-// forward kernel for op on n matrices.  Returns an SVD2_* code.
-template <typename T, bool CPLX, bool FLAG>
+// Validate the arguments, fill p and launch the forward kernel for op on n
+// matrices.  Returns an SVD2_* code.
+template <typename T, bool CPLX>
 inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *const *Vo, T *smax,
                       T *smin, int32_t *s, uint32_t flags, cudaStream_t stream,
                       FwdArgs<T, CPLX ? 8 : 4> &p) {
@@ -165,7 +147,7 @@ inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *con
   p.flags = flags;
   Launch L = get_launch(op);
   if (!vec_ok) L.mpt = 1;
-  FwdKernel<T, CPLX, FLAG> k = pick_kernel<T, CPLX, FLAG>(L.mpt, L.unroll);
+  FwdKernel<T, CPLX> k = pick_kernel<T, CPLX>(L.mpt, L.unroll);
   if (!k) return SVD2_EINVAL;
   int resident = 0;
   SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, L.block, 0));

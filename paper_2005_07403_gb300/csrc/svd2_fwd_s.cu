@@ -8,6 +8,6 @@ extern "C" int svd2_batch_s(int64_t n, const float *const A[4], float *const U[4
                             float *const V[4], float *smax, float *smin, int32_t *s,
                             uint32_t flags, svd2_stream_t stream) {
   FwdArgs<float, 4> p{};
-  return launch_fwd<float, false, false>(kOpS, n, A, U, V, smax, smin, s, flags, (cudaStream_t)stream,
+  return launch_fwd<float, false>(kOpS, n, A, U, V, smax, smin, s, flags, (cudaStream_t)stream,
                                     p);
 }

@@ -11,9 +11,10 @@
 // (SMs x resident blocks) CTAs walks the tiles in a fixed round-robin order,
 // CTA c taking tiles c, c + grid, c + 2 grid, ...: no atomics, no scratch
 // memory, the same assignment on every launch, so the launch can be captured
-// once in a CUDA graph and replayed every step.  A tile's kind (real or
-// complex double) is uniform over the CTA, so the branch between the two
-// method variants never diverges inside a warp.
+// once in a CUDA graph and replayed every step.  Real and complex batches form
+// two tile sequences, each walked by its own persistent kernel (launched one
+// after the other), so each kernel carries only its own variant of the method
+// and keeps its own register budget.
 #include <new>
 
 #include "svd2_common.cuh"
@@ -36,12 +37,16 @@ struct MultiBatch {
   int32_t *s;
 };
 
-// Plan header, then nbatch MultiBatch records.
+// Plan header, then nbatch MultiBatch records: the nreal real batches first,
+// then the complex ones, each kind with its own tile sequence from 0.
 struct MultiPlanHeader {
   int32_t nbatch;
+  int32_t nreal;
   int32_t tile_matrices;   // matrices per tile = block * mpt * unroll
-  int64_t total_tiles;
-  int32_t block, mpt, unroll, pad;
+  int32_t block;
+  int64_t tiles_real;
+  int64_t tiles_cplx;
+  int32_t mpt, unroll;
 };
 constexpr size_t kPlanHeader = 64;
 
@@ -112,39 +117,35 @@ __device__ __forceinline__ void multi_group(const MultiBatch &b, int64_t k0, int
   }
 }
 
-template <int M, int UNR>
-__global__ void __launch_bounds__(512) multi_kernel(const unsigned char *plan) {
+template <bool CPLX, int M, int UNR>
+__global__ void __launch_bounds__(512, CPLX ? 2 : 1) multi_kernel(const unsigned char *plan) {
   const MultiPlanHeader &h = *reinterpret_cast<const MultiPlanHeader *>(plan);
   const MultiBatch *batches = reinterpret_cast<const MultiBatch *>(plan + kPlanHeader);
-  const int nbatch = h.nbatch;
-  const int64_t total = h.total_tiles;
+  const int b_end = CPLX ? h.nbatch : h.nreal;
+  const int64_t total = CPLX ? h.tiles_cplx : h.tiles_real;
   const int64_t per_tile = (int64_t)blockDim.x * M * UNR;
   if (h.tile_matrices != per_tile) return;   // launched with another shape than planned
-  int bi = 0;   // batch of the current tile; tiles only increase, so walk forward
+  int bi = CPLX ? h.nreal : 0;   // batch of the current tile; tiles only increase
   for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-    while (bi + 1 < nbatch && batches[bi + 1].tile0 <= t) ++bi;
+    while (bi + 1 < b_end && batches[bi + 1].tile0 <= t) ++bi;
     const MultiBatch &b = batches[bi];
     const int64_t base = (t - b.tile0) * per_tile;
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
       const int64_t k0 = base + ((int64_t)r * blockDim.x + threadIdx.x) * M;
-      if (k0 < b.n) {
-        if (b.kind == SVD2_KIND_Z)
-          multi_group<true, M>(b, k0, b.n);
-        else
-          multi_group<false, M>(b, k0, b.n);
-      }
+      if (k0 < b.n) multi_group<CPLX, M>(b, k0, b.n);
     }
   }
 }
 
 using MultiKernel = void (*)(const unsigned char *);
 
+template <bool CPLX>
 static MultiKernel pick_multi(int mpt, int unroll) {
-  if (mpt == 1 && unroll == 1) return multi_kernel<1, 1>;
-  if (mpt == 1 && unroll == 2) return multi_kernel<1, 2>;
-  if (mpt == 2 && unroll == 1) return multi_kernel<2, 1>;
-  if (mpt == 2 && unroll == 2) return multi_kernel<2, 2>;
+  if (mpt == 1 && unroll == 1) return multi_kernel<CPLX, 1, 1>;
+  if (mpt == 1 && unroll == 2) return multi_kernel<CPLX, 1, 2>;
+  if (mpt == 2 && unroll == 1) return multi_kernel<CPLX, 2, 1>;
+  if (mpt == 2 && unroll == 2) return multi_kernel<CPLX, 2, 2>;
   return nullptr;
 }
 
@@ -161,7 +162,7 @@ extern "C" int svd2_multi_prepare(const svd2_batch_desc *descs, int32_t nbatch, 
                                   int mpt, int unroll, void *plan, size_t plan_bytes,
                                   int64_t *total_tiles) {
   if (nbatch < 0 || !plan || (nbatch > 0 && !descs)) return SVD2_EINVAL;
-  if (block < 32 || block > 512 || block % 32 || !pick_multi(mpt, unroll)) return SVD2_EINVAL;
+  if (block < 32 || block > 512 || block % 32 || !pick_multi<false>(mpt, unroll)) return SVD2_EINVAL;
   if (plan_bytes < svd2_multi_plan_bytes(nbatch) || !aligned(plan, 16)) return SVD2_EINVAL;
   const int64_t per_tile = (int64_t)block * mpt * unroll;
   unsigned char *host = new (std::nothrow) unsigned char[svd2_multi_plan_bytes(nbatch)];
@@ -172,10 +173,15 @@ extern "C" int svd2_multi_prepare(const svd2_batch_desc *descs, int32_t nbatch, 
   h.block = block;
   h.mpt = mpt;
   h.unroll = unroll;
-  int64_t tiles = 0;
+  int64_t tiles_of[2] = {0, 0};
+  int32_t nreal = 0;
+  for (int32_t i = 0; i < nbatch; ++i) nreal += descs[i].kind == SVD2_KIND_Z ? 0 : 1;
+  int32_t slot_of[2] = {0, nreal};   // next record of each kind
   MultiBatch *mb = reinterpret_cast<MultiBatch *>(host + kPlanHeader);
   for (int32_t i = 0; i < nbatch; ++i) {
     const svd2_batch_desc &d = descs[i];
+    const int kz = d.kind == SVD2_KIND_Z ? 1 : 0;
+    int64_t &tiles = tiles_of[kz];
     const int na = d.kind == SVD2_KIND_Z ? 8 : 4;
     if ((d.kind != SVD2_KIND_D && d.kind != SVD2_KIND_Z) || d.n < 0 ||
         (d.flags & ~SVD2_BACKSCALE)) {
@@ -203,16 +209,18 @@ extern "C" int svd2_multi_prepare(const svd2_batch_desc *descs, int32_t nbatch, 
       delete[] host;
       return SVD2_EINVAL;
     }
-    mb[i] = b;
+    mb[slot_of[kz]++] = b;
     tiles += (d.n + per_tile - 1) / per_tile;
   }
-  h.total_tiles = tiles;
+  h.nreal = nreal;
+  h.tiles_real = tiles_of[0];
+  h.tiles_cplx = tiles_of[1];
   std::memcpy(host, &h, sizeof(h));
   const cudaError_t e = cudaMemcpy(plan, host, svd2_multi_plan_bytes(nbatch),
                                    cudaMemcpyHostToDevice);
   delete[] host;
   if (e != cudaSuccess) return record_cuda_error(e);
-  if (total_tiles) *total_tiles = tiles;
+  if (total_tiles) *total_tiles = tiles_of[0] + tiles_of[1];
   return SVD2_OK;
 }
 
@@ -226,44 +234,50 @@ static int multi_grid(MultiKernel k, int block, int grid, int *out) {
   return SVD2_OK;
 }
 
-extern "C" int svd2_multi_run(const void *plan, int block, int mpt, int unroll, int grid,
-                              svd2_stream_t stream) {
-  if (!plan || !aligned(plan, 16)) return SVD2_EINVAL;
-  MultiKernel k = pick_multi(mpt, unroll);
-  if (!k || block < 32 || block > 512 || block % 32 || grid < 0) return SVD2_EINVAL;
-  int g = 0;
-  const int rc = multi_grid(k, block, grid, &g);
+// The real-batch kernel, then the complex-batch kernel, on one stream.
+static int multi_launch(const void *plan, int block, int mpt, int unroll, int grid,
+                        cudaStream_t st) {
+  const MultiKernel kr = pick_multi<false>(mpt, unroll), kz = pick_multi<true>(mpt, unroll);
+  if (!kr || !kz || block < 32 || block > 512 || block % 32 || grid < 0) return SVD2_EINVAL;
+  int gr = 0, gz = 0;
+  int rc = multi_grid(kr, block, grid, &gr);
+  if (rc == SVD2_OK) rc = multi_grid(kz, block, grid, &gz);
   if (rc != SVD2_OK) return rc;
-  k<<<g, block, 0, (cudaStream_t)stream>>>(static_cast<const unsigned char *>(plan));
+  kr<<<gr, block, 0, st>>>(static_cast<const unsigned char *>(plan));
+  SVD2_CUDA_TRY(cudaGetLastError());
+  kz<<<gz, block, 0, st>>>(static_cast<const unsigned char *>(plan));
   SVD2_CUDA_TRY(cudaGetLastError());
   return SVD2_OK;
 }
 
-// The persistent launch captured once into an executable CUDA graph, for
+extern "C" int svd2_multi_run(const void *plan, int block, int mpt, int unroll, int grid,
+                              svd2_stream_t stream) {
+  if (!plan || !aligned(plan, 16)) return SVD2_EINVAL;
+  return multi_launch(plan, block, mpt, unroll, grid, (cudaStream_t)stream);
+}
+
+// The persistent launches captured once into an executable CUDA graph, for
 // replay at every step (the plan's batch pointers stay fixed while the data
 // in them changes).
 extern "C" int svd2_multi_graph_create(const void *plan, int block, int mpt, int unroll, int grid,
                                        void **graph_exec) {
   if (!graph_exec || !plan || !aligned(plan, 16)) return SVD2_EINVAL;
-  MultiKernel k = pick_multi(mpt, unroll);
-  if (!k || block < 32 || block > 512 || block % 32 || grid < 0) return SVD2_EINVAL;
-  int g = 0;
-  int rc = multi_grid(k, block, grid, &g);
-  if (rc != SVD2_OK) return rc;
+  if (!pick_multi<false>(mpt, unroll) || block < 32 || block > 512 || block % 32 || grid < 0)
+    return SVD2_EINVAL;
   cudaStream_t cs = nullptr;
   SVD2_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int rc = SVD2_OK;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    k<<<g, block, 0, cs>>>(static_cast<const unsigned char *>(plan));
-    const cudaError_t el = cudaGetLastError();
+    rc = multi_launch(plan, block, mpt, unroll, grid, cs);
     e = cudaStreamEndCapture(cs, &graph);
-    if (e == cudaSuccess) e = el;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess && rc == SVD2_OK) e = cudaGraphInstantiate(&exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(cs);
+  if (rc != SVD2_OK) return rc;
   if (e != cudaSuccess) return record_cuda_error(e);
   *graph_exec = exec;
   return SVD2_OK;

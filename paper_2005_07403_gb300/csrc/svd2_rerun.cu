@@ -1,76 +1,178 @@
 // FP32 form with FP64 re-run: svd2_batch_s_rerun / svd2_batch_c_rerun.
 //
-// Pass 1 is the single-precision method (Sec. 1, Sec. 7) over all matrices;
-// it flags every matrix whose scaled singular values satisfy
+// One kernel.  Each block takes tiles of consecutive matrices; for a tile it
+// first runs the single-precision method (Sec. 1, Sec. 7) on every matrix and
+// flags each matrix whose scaled singular values satisfy
 // sigma'_min < 2^tau sigma'_max (compared in float; the product by the power of
-// two is exact) and appends its index to a list in the workspace with one
-// atomic per warp.  Pass 2 re-runs the flagged matrices only, on full warps,
-// with the double-precision method on the exactly widened input, and writes
-// the double results rounded to float, sigma' brought to the float run's
-// scale: sigma'_32 = RN32(sigma'_64 2^(s32 - s64)).  Both passes run on the
-// caller's stream with no host synchronisation; pass 2 reads the list length
-// from device memory and covers it with a grid-stride loop.
+// two is exact), queueing its index and input elements in shared memory.
+// After a barrier the whole block re-runs the queued matrices, on full warps,
+// with the double-precision method on the exactly widened input, and
+// overwrites their outputs with the double results rounded to float, sigma'
+// brought to the float run's scale: sigma'_32 = RN32(sigma'_64 2^(s32 - s64)).
+// The re-run reads its inputs from shared memory and writes lines the block
+// has just written (still in L2), so it adds no scattered DRAM traffic.  The
+// number of re-run matrices is accumulated in the workspace.
 #include "svd2_fwd_impl.cuh"
 
 namespace svd2 {
 
-// Workspace layout: [0] total re-run count of the call (uint64), [1] count of
-// the current chunk (uint64), then from byte 256 the uint32 index list of the
-// current chunk (chunk-relative indices).
+// Workspace layout: [0] re-run count of the call (uint64).  The size formula
+// (256 bytes plus 4 per matrix) also leaves room for an index list, which this
+// single-kernel form keeps in shared memory instead.
 constexpr size_t kListOffset = 256;
 constexpr int64_t kChunk = int64_t(1) << 31;
 
-template <int NA>
-struct RerunArgs {
-  const float *a[NA];
-  float *u[NA];
-  float *v[NA];
-  float *smax;
-  float *smin;
-  const uint32_t *list;
-  const unsigned long long *count;
-  unsigned long long *total;
-  uint32_t flags;
-};
-
+// Re-run of one queued matrix in double precision; float outputs.
 template <bool CPLX>
-__global__ void __launch_bounds__(256) rerun_kernel(const RerunArgs<CPLX ? 8 : 4> p) {
+__device__ __forceinline__ void rerun_one(const FwdArgs<float, CPLX ? 8 : 4> &p, uint32_t k,
+                                          const float *a) {
   constexpr int NA = CPLX ? 8 : 4;
-  const unsigned long long cnt = *p.count;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (unsigned long long i = tid; i < cnt; i += stride) {
-    const uint32_t k = p.list[i];
-    float a[NA];
-    double ad[NA];
-    unsigned mx = 0;
+  double ad[NA];
+  unsigned mx = 0;
 #pragma unroll
-    for (int e = 0; e < NA; ++e) {
-      a[e] = p.a[e][k];
-      ad[e] = (double)a[e];
-      const unsigned b = fp<float>::bits(a[e]) & fp<float>::kAbs;
-      mx = b > mx ? b : mx;
-    }
-    int32_t s32 = scale_exponent<float>(mx);
-    double u[NA], v[NA], sx, sn;
-    int32_t s64;
+  for (int e = 0; e < NA; ++e) {
+    ad[e] = (double)a[e];
+    const unsigned b = fp<float>::bits(a[e]) & fp<float>::kAbs;
+    mx = b > mx ? b : mx;
+  }
+  int32_t s32 = scale_exponent<float>(mx);
+  double u[NA], v[NA], sx, sn;
+  int32_t s64;
+  int piv;
+  if constexpr (CPLX)
+    svd2_cplx<double>(ad, u, v, sx, sn, s64, piv);
+  else
+    svd2_real<double>(ad, u, v, sx, sn, s64, piv);
+  float fx = __double2float_rn(scalef(sx, s32 - s64));
+  float fn = __double2float_rn(scalef(sn, s32 - s64));
+  if (p.flags & SVD2_BACKSCALE) backscale(fx, fn, s32);
+#pragma unroll
+  for (int e = 0; e < NA; ++e) {
+    p.u[e][k] = __double2float_rn(u[e]);
+    p.v[e][k] = __double2float_rn(v[e]);
+  }
+  p.smax[k] = fx;
+  p.smin[k] = fn;
+}
+
+// The single-precision method on M matrices from k0, queueing the flagged ones.
+template <bool CPLX, int M>
+__device__ __forceinline__ void fp32_group(const FwdArgs<float, CPLX ? 8 : 4> &p, int64_t k0,
+                                           const float (&in)[CPLX ? 8 : 4][M], uint32_t *q_idx,
+                                           float *q_a, int qcap, int *q_n) {
+  constexpr int NA = CPLX ? 8 : 4;
+  float uo[NA][M], vo[NA][M], sx[M], sn[M];
+  int32_t so[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    float a[NA], u[NA], v[NA];
+#pragma unroll
+    for (int e = 0; e < NA; ++e) a[e] = in[e][m];
     int piv;
     if constexpr (CPLX)
-      svd2_cplx<double>(ad, u, v, sx, sn, s64, piv);
+      svd2_cplx<float>(a, u, v, sx[m], sn[m], so[m], piv);
     else
-      svd2_real<double>(ad, u, v, sx, sn, s64, piv);
-    float fx = __double2float_rn(scalef(sx, s32 - s64));
-    float fn = __double2float_rn(scalef(sn, s32 - s64));
-    if (p.flags & SVD2_BACKSCALE) backscale(fx, fn, s32);
+      svd2_real<float>(a, u, v, sx[m], sn[m], so[m], piv);
+    if (sn[m] < fp<float>::mul(p.tau, sx[m])) {
+      const int pos = atomicAdd(q_n, 1);      // shared memory; pos < qcap (one slot per matrix)
+      q_idx[pos] = (uint32_t)(k0 + m);
+#pragma unroll
+      for (int e = 0; e < NA; ++e) q_a[e * qcap + pos] = a[e];
+    }
+    if (p.flags & SVD2_BACKSCALE) backscale(sx[m], sn[m], so[m]);
 #pragma unroll
     for (int e = 0; e < NA; ++e) {
-      p.u[e][k] = __double2float_rn(u[e]);
-      p.v[e][k] = __double2float_rn(v[e]);
+      uo[e][m] = u[e];
+      vo[e][m] = v[e];
     }
-    p.smax[k] = fx;
-    p.smin[k] = fn;
   }
-  if (tid == 0) *p.total += cnt;
+#pragma unroll
+  for (int e = 0; e < NA; ++e) store_vec<float, M>(p.u[e] + k0, uo[e]);
+#pragma unroll
+  for (int e = 0; e < NA; ++e) store_vec<float, M>(p.v[e] + k0, vo[e]);
+  store_vec<float, M>(p.smax + k0, sx);
+  store_vec<float, M>(p.smin + k0, sn);
+  store_vec<int32_t, M>(p.s + k0, so);
+}
+
+// Drain the block's queue -- every queued matrix re-run in double precision --
+// once it holds at least `min_fill` entries (0: whatever it holds).  Called by
+// every thread of the block; the decision is uniform.
+template <bool CPLX>
+__device__ __forceinline__ void drain(const FwdArgs<float, CPLX ? 8 : 4> &p, const uint32_t *q_idx,
+                                      const float *q_a, int qcap, int *q_n, int min_fill) {
+  constexpr int NA = CPLX ? 8 : 4;
+  __syncthreads();
+  const int qn = *q_n;
+  if (qn == 0 || qn < min_fill) return;
+  for (int i = threadIdx.x; i < qn; i += blockDim.x) {
+    float a[NA];
+#pragma unroll
+    for (int e = 0; e < NA; ++e) a[e] = q_a[e * qcap + i];
+    rerun_one<CPLX>(p, q_idx[i], a);
+  }
+  if (threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)qn);
+  __syncthreads();
+  if (threadIdx.x == 0) *q_n = 0;
+  __syncthreads();
+}
+
+// Tiles of blockDim * M * UNR matrices; every thread of a block runs the same
+// number of tile iterations, so the barriers of drain() are uniform.  The
+// queue holds one tile plus one block of matrices and is drained when it has
+// a block's worth (full warps in the double-precision pass), and at the end.
+template <bool CPLX, int M, int UNR>
+__global__ void __launch_bounds__(512) fused_rerun_kernel(const FwdArgs<float, CPLX ? 8 : 4> p) {
+  constexpr int NA = CPLX ? 8 : 4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int qcap = blockDim.x * (M * UNR + 1);
+  int *q_n = reinterpret_cast<int *>(smem);
+  uint32_t *q_idx = reinterpret_cast<uint32_t *>(smem + 16);
+  float *q_a = reinterpret_cast<float *>(smem + 16 + (size_t)qcap * sizeof(uint32_t));
+  if (threadIdx.x == 0) *q_n = 0;
+  __syncthreads();
+  const int64_t ngroups = p.n / M;
+  const int64_t per_tile = (int64_t)blockDim.x * UNR;      // groups per tile
+  const int64_t ntiles = (ngroups + per_tile - 1) / per_tile;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    float in[UNR][NA][M];
+#pragma unroll
+    for (int r = 0; r < UNR; ++r) {
+      const int64_t g = t * per_tile + (int64_t)r * blockDim.x + threadIdx.x;
+      if (g < ngroups) {
+#pragma unroll
+        for (int e = 0; e < NA; ++e) load_vec<float, M>(p.a[e] + g * M, in[r][e]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < UNR; ++r) {
+      const int64_t g = t * per_tile + (int64_t)r * blockDim.x + threadIdx.x;
+      if (g < ngroups) fp32_group<CPLX, M>(p, g * M, in[r], q_idx, q_a, qcap, q_n);
+    }
+    drain<CPLX>(p, q_idx, q_a, qcap, q_n, blockDim.x);
+  }
+  // the n mod M tail, one matrix per thread of block 0
+  const int64_t tail = p.n - ngroups * M;
+  if (blockIdx.x == 0 && tail > 0 && threadIdx.x < tail) {
+    const int64_t k = ngroups * M + threadIdx.x;
+    float in1[NA][1];
+#pragma unroll
+    for (int e = 0; e < NA; ++e) in1[e][0] = p.a[e][k];
+    fp32_group<CPLX, 1>(p, k, in1, q_idx, q_a, qcap, q_n);
+  }
+  drain<CPLX>(p, q_idx, q_a, qcap, q_n, 0);
+}
+
+using FusedKernel4 = void (*)(const FwdArgs<float, 4>);
+using FusedKernel8 = void (*)(const FwdArgs<float, 8>);
+
+template <bool CPLX>
+static auto pick_fused(int mpt, int unroll) -> void (*)(const FwdArgs<float, CPLX ? 8 : 4>) {
+#define SVD2_PICK(M_, U_) \
+  if (mpt == M_ && unroll == U_) return fused_rerun_kernel<CPLX, M_, U_>;
+  SVD2_PICK(1, 1) SVD2_PICK(1, 2) SVD2_PICK(2, 1) SVD2_PICK(2, 2) SVD2_PICK(4, 1) SVD2_PICK(4, 2)
+#undef SVD2_PICK
+  return nullptr;
 }
 
 template <bool CPLX>
@@ -82,49 +184,43 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
   if (n == 0) return SVD2_OK;
   if (!workspace || !aligned(workspace, 16) || ws_bytes < svd2_rerun_workspace_bytes(n))
     return SVD2_EINVAL;
-  if (!A || !U || !V) return SVD2_EINVAL;
-  auto *ws = static_cast<unsigned char *>(workspace);
-  auto *total = reinterpret_cast<unsigned long long *>(ws);
-  auto *count = total + 1;
-  auto *list = reinterpret_cast<uint32_t *>(ws + kListOffset);
-  SVD2_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(unsigned long long), stream));
-  // pass 2 covers a device-resident count with a grid-stride loop: one
-  // resident wave of blocks, enough warps to hide its scattered accesses
+  if (!A || !U || !V || !smax || !smin || !s) return SVD2_EINVAL;
+  auto *count = static_cast<unsigned long long *>(workspace);
+  SVD2_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream));
+  Launch L = get_launch(op);
+  bool vec_ok = aligned(smax, 16) && aligned(smin, 16) && aligned(s, 16);
+  for (int e = 0; e < NA; ++e) {
+    if (!A[e] || !U[e] || !V[e]) return SVD2_EINVAL;
+    vec_ok = vec_ok && aligned(A[e], 16) && aligned(U[e], 16) && aligned(V[e], 16);
+  }
+  if (!vec_ok) L.mpt = 1;
+  auto k = pick_fused<CPLX>(L.mpt, L.unroll);
+  if (!k) return SVD2_EINVAL;
+  const size_t qcap = (size_t)L.block * (L.mpt * L.unroll + 1);
+  const size_t shmem = 16 + qcap * sizeof(uint32_t) + qcap * NA * sizeof(float);
+  SVD2_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
   int resident = 0;
-  SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, rerun_kernel<CPLX>, 256, 0));
-  const int grid2 = sm_count() * (resident > 0 ? resident : 1);
+  SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, L.block, shmem));
   for (int64_t base = 0; base < n; base += kChunk) {
     const int64_t m = (n - base < kChunk) ? (n - base) : kChunk;
-    const float *a[NA];
-    float *u[NA], *v[NA];
-    for (int e = 0; e < NA; ++e) {
-      if (!A[e] || !U[e] || !V[e]) return SVD2_EINVAL;
-      a[e] = A[e] + base;
-      u[e] = U[e] + base;
-      v[e] = V[e] + base;
-    }
-    if (!smax || !smin || !s) return SVD2_EINVAL;
-    SVD2_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream));
     FwdArgs<float, NA> p{};
-    p.tau = ldexpf(1.0f, tau_log2);
-    p.list = list;
-    p.count = count;
-    int rc = launch_fwd<float, CPLX, true>(op, m, a, u, v, smax + base, smin + base, s + base,
-                                           flags, stream, p);
-    if (rc != SVD2_OK) return rc;
-    RerunArgs<NA> q{};
     for (int e = 0; e < NA; ++e) {
-      q.a[e] = a[e];
-      q.u[e] = u[e];
-      q.v[e] = v[e];
+      p.a[e] = A[e] + base;
+      p.u[e] = U[e] + base;
+      p.v[e] = V[e] + base;
     }
-    q.smax = smax + base;
-    q.smin = smin + base;
-    q.list = list;
-    q.count = count;
-    q.total = total;
-    q.flags = flags;
-    rerun_kernel<CPLX><<<grid2, 256, 0, stream>>>(q);
+    p.smax = smax + base;
+    p.smin = smin + base;
+    p.s = s + base;
+    p.n = m;
+    p.flags = flags;
+    p.tau = ldexpf(1.0f, tau_log2);
+    p.count = count;
+    const int64_t tiles = (m / L.mpt + (int64_t)L.block * L.unroll - 1) / ((int64_t)L.block * L.unroll);
+    const int64_t cap = (int64_t)sm_count() * (resident > 0 ? resident : 1) * (L.waves > 0 ? L.waves : 1 << 20);
+    int64_t grid = tiles < 1 ? 1 : tiles;
+    if (grid > cap) grid = cap;
+    k<<<(unsigned)grid, L.block, shmem, stream>>>(p);
     SVD2_CUDA_TRY(cudaGetLastError());
   }
   return SVD2_OK;
