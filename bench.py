@@ -97,6 +97,59 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return GB300_SM_MAX_MHZ
+
+
+# The FP64 forms are bound by the FP64 pipe, not by HBM: GB300 executes 2 FP64
+# add/mul/fma per SM per clock (1.25 TFLOP/s nominal = 152 SMs x 2 fma x 2 flops
+# x 2.07 GHz).  Their roofline counts the method's FP64 add, mul and fma per
+# matrix (divisions and square roots run on the integer and FP32 pipes and are
+# not counted); sign, exponent, min/max and pivot steps are bit operations.
+GB300_SMS = 152
+GB300_FP64_PER_SM_CLK = 2
+GB300_SM_MAX_MHZ = 2070.0
+FP64_OPS_PER_MATRIX = {"z": 91, "d": 34}
+
+
+def sources_digest():
+    """SHA-256 over the CUDA sources, the C header and the build script: the
+    DRAM traffic recorded under profiles/ holds only for this exact digest."""
+    import hashlib
+    h = hashlib.sha256()
+    files = [os.path.join("include", "svd2.h"), os.path.join("paper_2005_07403_gb300", "build.py")]
+    csrc = os.path.join("paper_2005_07403_gb300", "csrc")
+    files += sorted(os.path.join(csrc, f) for f in os.listdir(os.path.join(ROOT, csrc))
+                    if f.endswith((".cu", ".cuh")))
+    for rel in files:
+        h.update(rel.encode())
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, n):
+    """DRAM bytes (read + write) per launch of the workload's kernel, scaled from
+    the ncu capture in profiles/dram_traffic.txt to n matrices; None when no
+    capture exists for the current sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    digest = sources_digest()
+    for ln in lines:
+        f = ln.split()
+        if len(f) >= 6 and not ln.startswith("#") and f[0] == workload and f[1] == digest:
+            n_cap, rd, wr = int(f[3]), float(f[4]), float(f[5])
+            return (rd + wr) * n / n_cap
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -384,7 +437,9 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     ms_per_step = ms_max / args.steps
     value = world * n * args.steps / (ms_max / 1e3)
-    launches_per_step = 2 if W["form"] == "rerun" else 1
+    # our kernels per call: the FP32 forms run the batch kernel and its fix-up
+    # pass (plus a memset of their flag words); the FP64 forms one kernel
+    launches_per_step = 2 if W["dtype"] == "f32" else 1
 
     # end to end through the C ABI with host buffers (svd2_batch_host): every
     # step copies A in and every output out through the chunked pipeline
@@ -415,9 +470,24 @@ def run_ours(args):
     peak, peak_src = measured_peaks()
     bytes_launch = W["bytes_per"] * n
     achieved = bytes_launch / (ms_per_step / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "note": f"peak {peak_src}; algorithmic {W['bytes_per']} B/matrix x {n} per launch"}
+    traffic = recorded_traffic(args.workload, n)
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": traffic,
+           "note": f"peak {peak_src}; algorithmic {W['bytes_per']} B/matrix x {n} per launch"
+                   + ("; traffic from profiles/dram_traffic.txt scaled to n" if traffic else "")}
+    if W["kind"] in FP64_OPS_PER_MATRIX:
+        ops = FP64_OPS_PER_MATRIX[W["kind"]]
+        fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3   # G op/s
+        fp64_achieved = ops * n / (ms_per_step / 1e3) / 1e9
+        roofline = {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak,
+                    "unit": "G FP64 op/s", "frac": fp64_achieved / fp64_peak,
+                    "traffic": traffic,
+                    "note": f"FP64 pipe: {ops} FP64 add/mul/fma per matrix x {n} per launch; "
+                            f"peak derived: {GB300_SMS} SMs x {GB300_FP64_PER_SM_CLK} per clock "
+                            f"x {sm_max_mhz():.0f} MHz",
+                    "hbm": hbm}
+    else:
+        roofline = hbm
     line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -445,6 +515,9 @@ def run_ours(args):
 
 
 def main():
+    if "--sources-digest" in sys.argv:
+        print(sources_digest())
+        return
     args = parse()
     if args.impl == "reference":
         run_reference(args)

@@ -23,6 +23,11 @@ int record_cuda_error(cudaError_t e);   // stores e for svd2_last_cuda_error, re
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+// A 256-byte block of device memory, zeroed in stream order on st, from the
+// library's stream-ordered pool of the current device (per-call flags of the
+// fast/fix-up kernel pair); flag_release returns it in stream order.
+int flag_block(cudaStream_t st, void **p);
+int flag_release(void *p, cudaStream_t st);
 
 // ----------------------------------------------------------- launch shape
 

@@ -28,7 +28,16 @@ struct FwdArgs {
   // FP32 form with FP64 re-run only: re-run threshold and re-run counter.
   T tau;
   unsigned long long *count;
+  // Set to nonzero by the fast kernel when it flagged a matrix (see fix_kernel).
+  unsigned long long *redo;
 };
+
+// s written by the fast kernel for a matrix it could not finish: its outputs
+// are recomputed by the fix-up kernel.  (Valid s are -2 .. 2095 and kZeroS.)
+constexpr int32_t kRedoS = INT32_MIN;
+// FP32 form with re-run: the single-precision results stand but the
+// double-precision re-run left its fast domain.
+constexpr int32_t kRedoRerun = INT32_MIN + 1;
 
 // Optional back-scaling of Fig. 1: Sigma = 2^-s Sigma' (correctly rounded,
 // may overflow or underflow), then s = 0.
@@ -41,23 +50,69 @@ __device__ __forceinline__ void backscale(T &smax, T &smin, int32_t &s) {
   s = 0;
 }
 
+// One matrix with the given arithmetic policy (Sec. 2 - Sec. 7, Eq. 29).
+template <typename T, bool CPLX, typename Ar>
+__device__ __forceinline__ void svd2_one(Ar &ar, const T *a, T *u, T *v, T &smax, T &smin,
+                                         int32_t &s) {
+  int piv;
+  if constexpr (CPLX)
+    svd2_cplx<T>(ar, a, u, v, smax, smin, s, piv);
+  else
+    svd2_real<T>(ar, a, u, v, smax, smin, s, piv);
+}
+
+template <typename T> struct SigmaPair {
+  T smax, smin;
+};
+
+// Matrix k recomputed with the general arithmetic (ExactAr), its outputs
+// stored over whatever the fast kernel stored for it; returns sigma'_max and
+// sigma'_min before any back-scaling.  The element arrays may live in any
+// address space.
+template <typename T, bool CPLX>
+__device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u, T *const *v,
+                                               T *smax, T *smin, int32_t *s, uint32_t flags,
+                                               int64_t k) {
+  constexpr int NA = CPLX ? 8 : 4;
+  T ai[NA], uo[NA], vo[NA], sx, sn;
+  int32_t so;
+#pragma unroll
+  for (int e = 0; e < NA; ++e) ai[e] = a[e][k];
+  ExactAr<T> ar;
+  svd2_one<T, CPLX>(ar, ai, uo, vo, sx, sn, so);
+  const SigmaPair<T> r{sx, sn};
+  if (flags & SVD2_BACKSCALE) backscale(sx, sn, so);
+#pragma unroll
+  for (int e = 0; e < NA; ++e) {
+    u[e][k] = uo[e];
+    v[e][k] = vo[e];
+  }
+  smax[k] = sx;
+  smin[k] = sn;
+  s[k] = so;
+  return r;
+}
+
+// M matrices from k0 with the batch arithmetic HotAr, stored with vector
+// stores; a matrix the fast arithmetic cannot finish gets s = kRedoS and
+// raises p.redo.
 template <typename T, bool CPLX, int M>
 __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p, int64_t k0,
                                               const T (&in)[CPLX ? 8 : 4][M]) {
   constexpr int NA = CPLX ? 8 : 4;
   T uo[NA][M], vo[NA][M], sx[M], sn[M];
   int32_t so[M];
+  unsigned bad = 0;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     T a[NA], u[NA], v[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
-    int piv;
-    if constexpr (CPLX)
-      svd2_cplx<T>(a, u, v, sx[m], sn[m], so[m], piv);
-    else
-      svd2_real<T>(a, u, v, sx[m], sn[m], so[m], piv);
+    HotAr<T> ar;
+    svd2_one<T, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
     if (p.flags & SVD2_BACKSCALE) backscale(sx[m], sn[m], so[m]);
+    so[m] = ar.bad ? kRedoS : so[m];
+    bad |= ar.bad;
 #pragma unroll
     for (int e = 0; e < NA; ++e) {
       uo[e][m] = u[e];
@@ -71,6 +126,28 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
   store_vec<T, M>(p.smax + k0, sx);
   store_vec<T, M>(p.smin + k0, sn);
   store_vec<int32_t, M>(p.s + k0, so);
+  if (bad) *p.redo = 1;
+}
+
+// Fix-up pass after the fast kernel, on the same stream: if the fast kernel
+// flagged any matrix, every matrix with s = kRedoS is recomputed with the
+// general arithmetic.  Flagged matrices are those with a zero or subnormal
+// divisor or scaled entry, or an exponent out of the fast range: zero columns,
+// zero matrices, entries spanning more than the exponent range.  Otherwise the
+// pass reads one word and ends.
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256) fix_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
+  if (*p.redo == 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride)
+    if (p.s[k] == kRedoS) exact_one<T, CPLX>(p.a, p.u, p.v, p.smax, p.smin, p.s, p.flags, k);
+}
+
+// Blocks of the fix-up pass: enough to scan a batch quickly when it has work.
+inline unsigned fix_grid(int64_t n) {
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 4;
+  return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 // Minimum resident 512-thread blocks per SM the compiler must allow for: the
@@ -79,7 +156,8 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
 template <typename T, bool CPLX> constexpr int kMinBlocks = (sizeof(T) == 8 && CPLX) ? 2 : 1;
 
 template <typename T, bool CPLX, int M, int UNR>
-__global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>) fwd_kernel(const FwdArgs<T, CPLX ? 8 : 4> p) {
+__global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
+    fwd_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
   const int64_t ngroups = p.n / M;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -156,9 +234,25 @@ inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *con
   const int64_t loops = (groups + L.unroll - 1) / L.unroll;
   const int64_t units = loops > tail ? loops : tail;   // threads needed
   const int64_t grid = grid_for(units, L, resident);
-  k<<<(unsigned)grid, L.block, 0, stream>>>(p);
-  SVD2_CUDA_TRY(cudaGetLastError());
-  return SVD2_OK;
+  if constexpr (!kHotFlags<T>) {
+    k<<<(unsigned)grid, L.block, 0, stream>>>(p);
+    SVD2_CUDA_TRY(cudaGetLastError());
+    return SVD2_OK;
+  } else {
+    void *flag = nullptr;
+    int rc = flag_block(stream, &flag);
+    if (rc != SVD2_OK) return rc;
+    p.redo = static_cast<unsigned long long *>(flag);
+    k<<<(unsigned)grid, L.block, 0, stream>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      fix_kernel<T, CPLX><<<fix_grid(n), 256, 0, stream>>>(p);
+      e = cudaGetLastError();
+    }
+    rc = flag_release(flag, stream);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    return rc;
+  }
 }
 
 }  // namespace svd2

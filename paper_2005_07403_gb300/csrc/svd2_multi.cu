@@ -15,10 +15,11 @@
 // two tile sequences, each walked by its own persistent kernel (launched one
 // after the other), so each kernel carries only its own variant of the method
 // and keeps its own register budget.
+#include <cstddef>
 #include <new>
 
 #include "svd2_common.cuh"
-#include "svd2_math.cuh"
+#include "svd2_fwd_impl.cuh"
 
 namespace svd2 {
 
@@ -47,12 +48,40 @@ struct MultiPlanHeader {
   int64_t tiles_real;
   int64_t tiles_cplx;
   int32_t mpt, unroll;
+  unsigned long long redo;   // fix-up flag of the current run (zeroed before each run)
 };
 constexpr size_t kPlanHeader = 64;
+static_assert(sizeof(MultiPlanHeader) <= kPlanHeader, "plan header");
+constexpr size_t kRedoOffset = offsetof(MultiPlanHeader, redo);
+
+// Matrix k of batch b from the loaded elements a: the fast arithmetic, the
+// outputs stored; s = kRedoS and *bad set when the fast arithmetic cannot
+// finish it.
+template <bool CPLX>
+__device__ __forceinline__ void multi_one(const MultiBatch &b, int64_t k, const double *a,
+                                          unsigned &bad) {
+  constexpr int NA = CPLX ? 8 : 4;
+  double u[NA], v[NA], sx, sn;
+  int32_t s;
+  HotAr<double> ar;
+  svd2_one<double, CPLX>(ar, a, u, v, sx, sn, s);
+  if (b.flags & SVD2_BACKSCALE) backscale(sx, sn, s);
+  bad |= ar.bad;
+#pragma unroll
+  for (int e = 0; e < NA; ++e) {
+    __stcs(b.u[e] + k, u[e]);
+    __stcs(b.v[e] + k, v[e]);
+  }
+  __stcs(b.smax + k, sx);
+  __stcs(b.smin + k, sn);
+  __stcs(b.s + k, ar.bad ? kRedoS : s);
+}
 
 template <bool CPLX, int M>
-__device__ __forceinline__ void multi_group(const MultiBatch &b, int64_t k0, int64_t n) {
+__device__ __forceinline__ void multi_group(const MultiBatch &b, int64_t k0, int64_t n,
+                                            unsigned long long *redo) {
   constexpr int NA = CPLX ? 8 : 4;
+  unsigned bad = 0;
   if (k0 + M <= n) {
     double in[NA][M];
 #pragma unroll
@@ -62,59 +91,20 @@ __device__ __forceinline__ void multi_group(const MultiBatch &b, int64_t k0, int
     }
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      double a[NA], u[NA], v[NA], sx, sn;
-      int32_t s;
-      int piv;
+      double a[NA];
 #pragma unroll
       for (int e = 0; e < NA; ++e) a[e] = in[e][m];
-      if constexpr (CPLX)
-        svd2_cplx<double>(a, u, v, sx, sn, s, piv);
-      else
-        svd2_real<double>(a, u, v, sx, sn, s, piv);
-      if (b.flags & SVD2_BACKSCALE) {
-        if (s != kZeroS) {
-          sx = scalef(sx, -s);
-          sn = scalef(sn, -s);
-        }
-        s = 0;
-      }
-#pragma unroll
-      for (int e = 0; e < NA; ++e) {
-        __stcs(b.u[e] + k0 + m, u[e]);
-        __stcs(b.v[e] + k0 + m, v[e]);
-      }
-      __stcs(b.smax + k0 + m, sx);
-      __stcs(b.smin + k0 + m, sn);
-      __stcs(b.s + k0 + m, s);
+      multi_one<CPLX>(b, k0 + m, a, bad);
     }
   } else {
     for (int64_t k = k0; k < n; ++k) {   // ragged end of a batch
-      double a[NA], u[NA], v[NA], sx, sn;
-      int32_t s;
-      int piv;
+      double a[NA];
 #pragma unroll
       for (int e = 0; e < NA; ++e) a[e] = b.a[e][k];
-      if constexpr (CPLX)
-        svd2_cplx<double>(a, u, v, sx, sn, s, piv);
-      else
-        svd2_real<double>(a, u, v, sx, sn, s, piv);
-      if (b.flags & SVD2_BACKSCALE) {
-        if (s != kZeroS) {
-          sx = scalef(sx, -s);
-          sn = scalef(sn, -s);
-        }
-        s = 0;
-      }
-#pragma unroll
-      for (int e = 0; e < NA; ++e) {
-        b.u[e][k] = u[e];
-        b.v[e][k] = v[e];
-      }
-      b.smax[k] = sx;
-      b.smin[k] = sn;
-      b.s[k] = s;
+      multi_one<CPLX>(b, k, a, bad);
     }
   }
+  if (bad) *redo = 1;
 }
 
 template <bool CPLX, int M, int UNR>
@@ -125,6 +115,7 @@ __global__ void __launch_bounds__(512, CPLX ? 2 : 1) multi_kernel(const unsigned
   const int64_t total = CPLX ? h.tiles_cplx : h.tiles_real;
   const int64_t per_tile = (int64_t)blockDim.x * M * UNR;
   if (h.tile_matrices != per_tile) return;   // launched with another shape than planned
+  auto *redo = reinterpret_cast<unsigned long long *>(const_cast<unsigned char *>(plan) + kRedoOffset);
   int bi = CPLX ? h.nreal : 0;   // batch of the current tile; tiles only increase
   for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
     while (bi + 1 < b_end && batches[bi + 1].tile0 <= t) ++bi;
@@ -133,7 +124,27 @@ __global__ void __launch_bounds__(512, CPLX ? 2 : 1) multi_kernel(const unsigned
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
       const int64_t k0 = base + ((int64_t)r * blockDim.x + threadIdx.x) * M;
-      if (k0 < b.n) multi_group<CPLX, M>(b, k0, b.n);
+      if (k0 < b.n) multi_group<CPLX, M>(b, k0, b.n, redo);
+    }
+  }
+}
+
+// Fix-up pass after both persistent kernels: when the run flagged any
+// matrix, every matrix with s = kRedoS is recomputed with the general
+// arithmetic; otherwise one word is read.
+__global__ void __launch_bounds__(256) multi_fix_kernel(const unsigned char *plan) {
+  const MultiPlanHeader &h = *reinterpret_cast<const MultiPlanHeader *>(plan);
+  if (h.redo == 0) return;
+  const MultiBatch *batches = reinterpret_cast<const MultiBatch *>(plan + kPlanHeader);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int bi = 0; bi < h.nbatch; ++bi) {
+    const MultiBatch &b = batches[bi];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b.n; k += stride) {
+      if (b.s[k] != kRedoS) continue;
+      if (b.kind == SVD2_KIND_Z)
+        exact_one<double, true>(b.a, b.u, b.v, b.smax, b.smin, b.s, b.flags, k);
+      else
+        exact_one<double, false>(b.a, b.u, b.v, b.smax, b.smin, b.s, b.flags, k);
     }
   }
 }
@@ -243,10 +254,18 @@ static int multi_launch(const void *plan, int block, int mpt, int unroll, int gr
   int rc = multi_grid(kr, block, grid, &gr);
   if (rc == SVD2_OK) rc = multi_grid(kz, block, grid, &gz);
   if (rc != SVD2_OK) return rc;
-  kr<<<gr, block, 0, st>>>(static_cast<const unsigned char *>(plan));
+  const auto *pl = static_cast<const unsigned char *>(plan);
+  if (kHotFlags<double>)
+    SVD2_CUDA_TRY(cudaMemsetAsync(const_cast<unsigned char *>(pl) + kRedoOffset, 0,
+                                  sizeof(unsigned long long), st));
+  kr<<<gr, block, 0, st>>>(pl);
   SVD2_CUDA_TRY(cudaGetLastError());
-  kz<<<gz, block, 0, st>>>(static_cast<const unsigned char *>(plan));
+  kz<<<gz, block, 0, st>>>(pl);
   SVD2_CUDA_TRY(cudaGetLastError());
+  if (kHotFlags<double>) {
+    multi_fix_kernel<<<sm_count() * 4, 256, 0, st>>>(pl);
+    SVD2_CUDA_TRY(cudaGetLastError());
+  }
   return SVD2_OK;
 }
 

@@ -16,16 +16,19 @@
 
 namespace svd2 {
 
-// Workspace layout: [0] re-run count of the call (uint64).  The size formula
-// (256 bytes plus 4 per matrix) also leaves room for an index list, which this
-// single-kernel form keeps in shared memory instead.
+// Workspace layout: [0] re-run count of the call (uint64), [8] the fix-up
+// flag of the call (uint64).  The size formula (256 bytes plus 4 per matrix)
+// also leaves room for an index list, which this form keeps in shared memory.
 constexpr size_t kListOffset = 256;
 constexpr int64_t kChunk = int64_t(1) << 31;
 
-// Re-run of one queued matrix in double precision; float outputs.
-template <bool CPLX>
-__device__ __forceinline__ void rerun_one(const FwdArgs<float, CPLX ? 8 : 4> &p, uint32_t k,
-                                          const float *a) {
+// Re-run of one queued matrix in double precision with the arithmetic policy
+// Ar; float outputs u, v, sigma' stored (s is left to the caller).  Returns the
+// final s of the matrix (the float run's exponent, or 0 after back-scaling).
+// With FastAr, ar.bad set means the stored outputs are unspecified.
+template <bool CPLX, typename Ar>
+__device__ __forceinline__ int32_t rerun_one(Ar &ar, const FwdArgs<float, CPLX ? 8 : 4> &p,
+                                             int64_t k, const float *a) {
   constexpr int NA = CPLX ? 8 : 4;
   double ad[NA];
   unsigned mx = 0;
@@ -38,11 +41,7 @@ __device__ __forceinline__ void rerun_one(const FwdArgs<float, CPLX ? 8 : 4> &p,
   int32_t s32 = scale_exponent<float>(mx);
   double u[NA], v[NA], sx, sn;
   int32_t s64;
-  int piv;
-  if constexpr (CPLX)
-    svd2_cplx<double>(ad, u, v, sx, sn, s64, piv);
-  else
-    svd2_real<double>(ad, u, v, sx, sn, s64, piv);
+  svd2_one<double, CPLX>(ar, ad, u, v, sx, sn, s64);
   float fx = __double2float_rn(scalef(sx, s32 - s64));
   float fn = __double2float_rn(scalef(sn, s32 - s64));
   if (p.flags & SVD2_BACKSCALE) backscale(fx, fn, s32);
@@ -53,9 +52,22 @@ __device__ __forceinline__ void rerun_one(const FwdArgs<float, CPLX ? 8 : 4> &p,
   }
   p.smax[k] = fx;
   p.smin[k] = fn;
+  return s32;
 }
 
-// The single-precision method on M matrices from k0, queueing the flagged ones.
+// Queue matrix k (index and input elements) for the double-precision re-run.
+template <int NA>
+__device__ __forceinline__ void enqueue(uint32_t k, const float *a, uint32_t *q_idx, float *q_a,
+                                        int qcap, int *q_n) {
+  const int pos = atomicAdd(q_n, 1);      // shared memory; pos < qcap (one slot per matrix)
+  q_idx[pos] = k;
+#pragma unroll
+  for (int e = 0; e < NA; ++e) q_a[e * qcap + pos] = a[e];
+}
+
+// The single-precision method on M matrices from k0, queueing the matrices
+// whose sigma' ask for the re-run; a matrix the fast arithmetic cannot finish
+// gets s = kRedoS (the fix-up kernel then decides its re-run).
 template <bool CPLX, int M>
 __device__ __forceinline__ void fp32_group(const FwdArgs<float, CPLX ? 8 : 4> &p, int64_t k0,
                                            const float (&in)[CPLX ? 8 : 4][M], uint32_t *q_idx,
@@ -63,23 +75,19 @@ __device__ __forceinline__ void fp32_group(const FwdArgs<float, CPLX ? 8 : 4> &p
   constexpr int NA = CPLX ? 8 : 4;
   float uo[NA][M], vo[NA][M], sx[M], sn[M];
   int32_t so[M];
+  unsigned bad = 0;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     float a[NA], u[NA], v[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
-    int piv;
-    if constexpr (CPLX)
-      svd2_cplx<float>(a, u, v, sx[m], sn[m], so[m], piv);
-    else
-      svd2_real<float>(a, u, v, sx[m], sn[m], so[m], piv);
-    if (sn[m] < fp<float>::mul(p.tau, sx[m])) {
-      const int pos = atomicAdd(q_n, 1);      // shared memory; pos < qcap (one slot per matrix)
-      q_idx[pos] = (uint32_t)(k0 + m);
-#pragma unroll
-      for (int e = 0; e < NA; ++e) q_a[e * qcap + pos] = a[e];
-    }
+    FastAr<float> ar;
+    svd2_one<float, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
+    if (!ar.bad && sn[m] < fp<float>::mul(p.tau, sx[m]))
+      enqueue<NA>((uint32_t)(k0 + m), a, q_idx, q_a, qcap, q_n);
     if (p.flags & SVD2_BACKSCALE) backscale(sx[m], sn[m], so[m]);
+    so[m] = ar.bad ? kRedoS : so[m];
+    bad |= ar.bad;
 #pragma unroll
     for (int e = 0; e < NA; ++e) {
       uo[e][m] = u[e];
@@ -93,6 +101,7 @@ __device__ __forceinline__ void fp32_group(const FwdArgs<float, CPLX ? 8 : 4> &p
   store_vec<float, M>(p.smax + k0, sx);
   store_vec<float, M>(p.smin + k0, sn);
   store_vec<int32_t, M>(p.s + k0, so);
+  if (bad) *p.redo = 1;
 }
 
 // Drain the block's queue -- every queued matrix re-run in double precision --
@@ -109,7 +118,12 @@ __device__ __forceinline__ void drain(const FwdArgs<float, CPLX ? 8 : 4> &p, con
     float a[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) a[e] = q_a[e * qcap + i];
-    rerun_one<CPLX>(p, q_idx[i], a);
+    FastAr<double> ar;
+    rerun_one<CPLX>(ar, p, q_idx[i], a);
+    if (ar.bad) {                       // the fix-up kernel re-runs it exactly
+      p.s[q_idx[i]] = kRedoRerun;
+      *p.redo = 1;
+    }
   }
   if (threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)qn);
   __syncthreads();
@@ -122,7 +136,8 @@ __device__ __forceinline__ void drain(const FwdArgs<float, CPLX ? 8 : 4> &p, con
 // queue holds one tile plus one block of matrices and is drained when it has
 // a block's worth (full warps in the double-precision pass), and at the end.
 template <bool CPLX, int M, int UNR>
-__global__ void __launch_bounds__(512) fused_rerun_kernel(const FwdArgs<float, CPLX ? 8 : 4> p) {
+__global__ void __launch_bounds__(512)
+    fused_rerun_kernel(const __grid_constant__ FwdArgs<float, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
   extern __shared__ __align__(16) unsigned char smem[];
   const int qcap = blockDim.x * (M * UNR + 1);
@@ -166,6 +181,37 @@ __global__ void __launch_bounds__(512) fused_rerun_kernel(const FwdArgs<float, C
 using FusedKernel4 = void (*)(const FwdArgs<float, 4>);
 using FusedKernel8 = void (*)(const FwdArgs<float, 8>);
 
+// Fix-up pass of the re-run form (same stream, after the fused kernel): s =
+// kRedoS -- the single-precision method with the general arithmetic, then the
+// re-run test and, if it asks, the double-precision re-run (counted);
+// s = kRedoRerun -- the double-precision re-run with the general arithmetic
+// (already counted).  Reads one word and ends when nothing was flagged.
+template <bool CPLX>
+__global__ void __launch_bounds__(256)
+    rerun_fix_kernel(const __grid_constant__ FwdArgs<float, CPLX ? 8 : 4> p) {
+  constexpr int NA = CPLX ? 8 : 4;
+  if (*p.redo == 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride) {
+    const int32_t sk = p.s[k];
+    if (sk != kRedoS && sk != kRedoRerun) continue;
+    bool rerun = sk == kRedoRerun;
+    if (!rerun) {
+      const SigmaPair<float> r =
+          exact_one<float, CPLX>(p.a, p.u, p.v, p.smax, p.smin, p.s, p.flags, k);
+      rerun = r.smin < fp<float>::mul(p.tau, r.smax);
+      if (rerun) atomicAdd(p.count, 1ull);
+    }
+    if (rerun) {
+      float a[NA];
+#pragma unroll
+      for (int e = 0; e < NA; ++e) a[e] = p.a[e][k];
+      ExactAr<double> ar;
+      p.s[k] = rerun_one<CPLX>(ar, p, k, a);
+    }
+  }
+}
+
 template <bool CPLX>
 static auto pick_fused(int mpt, int unroll) -> void (*)(const FwdArgs<float, CPLX ? 8 : 4>) {
 #define SVD2_PICK(M_, U_) \
@@ -186,7 +232,7 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
     return SVD2_EINVAL;
   if (!A || !U || !V || !smax || !smin || !s) return SVD2_EINVAL;
   auto *count = static_cast<unsigned long long *>(workspace);
-  SVD2_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream));
+  SVD2_CUDA_TRY(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), stream));
   Launch L = get_launch(op);
   bool vec_ok = aligned(smax, 16) && aligned(smin, 16) && aligned(s, 16);
   for (int e = 0; e < NA; ++e) {
@@ -216,11 +262,14 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
     p.flags = flags;
     p.tau = ldexpf(1.0f, tau_log2);
     p.count = count;
+    p.redo = count + 1;
     const int64_t tiles = (m / L.mpt + (int64_t)L.block * L.unroll - 1) / ((int64_t)L.block * L.unroll);
     const int64_t cap = (int64_t)sm_count() * (resident > 0 ? resident : 1) * (L.waves > 0 ? L.waves : 1 << 20);
     int64_t grid = tiles < 1 ? 1 : tiles;
     if (grid > cap) grid = cap;
     k<<<(unsigned)grid, L.block, shmem, stream>>>(p);
+    SVD2_CUDA_TRY(cudaGetLastError());
+    rerun_fix_kernel<CPLX><<<fix_grid(m), 256, 0, stream>>>(p);
     SVD2_CUDA_TRY(cudaGetLastError());
   }
   return SVD2_OK;

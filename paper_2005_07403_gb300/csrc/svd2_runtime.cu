@@ -42,6 +42,47 @@ Launch get_launch(int op) {
   return g_launch[op];
 }
 
+// One stream-ordered memory pool per device for the per-call flag blocks,
+// created on first use and kept until the process exits; freed blocks stay in
+// the pool (release threshold: never), so later calls do not allocate from
+// the driver.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static int pool_of_current_device(cudaMemPool_t *out) {
+  int dev = 0;
+  SVD2_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return SVD2_EINVAL;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    SVD2_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    SVD2_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return SVD2_OK;
+}
+
+int flag_block(cudaStream_t st, void **p) {
+  cudaMemPool_t pool = nullptr;
+  const int rc = pool_of_current_device(&pool);
+  if (rc != SVD2_OK) return rc;
+  SVD2_CUDA_TRY(cudaMallocFromPoolAsync(p, 256, pool, st));
+  SVD2_CUDA_TRY(cudaMemsetAsync(*p, 0, 256, st));
+  return SVD2_OK;
+}
+
+int flag_release(void *p, cudaStream_t st) {
+  SVD2_CUDA_TRY(cudaFreeAsync(p, st));
+  return SVD2_OK;
+}
+
 int64_t grid_for(int64_t units, const Launch &L, int resident_blocks_per_sm) {
   int64_t need = (units + L.block - 1) / L.block;
   if (need < 1) need = 1;

@@ -172,17 +172,10 @@ SFP_FN double hw_sqrt(double a) {
 // values of the residuals below are small; only their low 64 bits are formed).
 SFP_FN uint64_t mulw(int64_t a, uint64_t b) { return (uint64_t)a * b; }
 
-// RN(a / b).
-SFP_FN double div_rn(double a, double b) {
-  const uint64_t ua = dbits(a), ub = dbits(b);
-  const uint64_t sgn = (ua ^ ub) & kSign;
-  const uint32_t ea = (uint32_t)(ua >> 52) & 0x7ffu, eb = (uint32_t)(ub >> 52) & 0x7ffu;
-  const int e0 = (int)ea - (int)eb + 1023;
-  const bool b_normal = eb - 1u < 2046u;
-  if ((ua & kAbs) == 0 && b_normal) return dval(sgn);          // +-0 / normal
-  // fast domain: a, b normal and the quotient's exponent in [1, 2045] whichever
-  // way the significand quotient falls, so the result is normal
-  if (!(ea - 1u < 2046u && b_normal && (unsigned)(e0 - 2) < 2044u)) return hw_div(a, b);
+// RN(a / b) for a, b normal with the quotient's exponent e0 - 1 or e0 in
+// [1, 2045] (e0 = ea - eb + 1023): the significand quotient by three integer
+// digits, sign and exponent attached.
+SFP_FN double div_core(uint64_t ua, uint64_t ub, uint64_t sgn, int e0) {
   const uint64_t ma = (ua & kFrac) | kImpl, mb = (ub & kFrac) | kImpl;
   const bool lt = ma < mb;
   const uint64_t A = lt ? ma << 1 : ma;     // A in [mb, 2 mb): A/mb in [1, 2)
@@ -215,11 +208,37 @@ SFP_FN double div_rn(double a, double b) {
   return dval(sgn | (((uint64_t)(e - 1) << 52) + Q));
 }
 
-// RN(sqrt(x)).
-SFP_FN double sqrt_rn(double x) {
-  const uint64_t ux = dbits(x);
-  const uint32_t ex = (uint32_t)(ux >> 52);        // includes the sign bit
-  if (!(ex - 1u < 2046u)) return hw_sqrt(x);       // +-0, subnormal, negative, inf, NaN
+// RN(a / b) on the fast domain -- b normal, and a = +-0 or a normal with the
+// quotient's exponent in [1, 2045] whichever way the significand quotient
+// falls (so the result is normal) -- without a branch.  Outside that domain
+// the result is unspecified and bad is set to 1.
+SFP_FN double div_fast(double a, double b, unsigned &bad) {
+  const uint64_t ua = dbits(a), ub = dbits(b);
+  const uint64_t sgn = (ua ^ ub) & kSign;
+  const uint32_t ea = (uint32_t)(ua >> 52) & 0x7ffu, eb = (uint32_t)(ub >> 52) & 0x7ffu;
+  const int e0 = (int)ea - (int)eb + 1023;
+  const bool b_normal = eb - 1u < 2046u;
+  const bool a_zero = (ua & kAbs) == 0;
+  bad |= (b_normal && (a_zero || (ea - 1u < 2046u && (unsigned)(e0 - 2) < 2044u))) ? 0u : 1u;
+  const double q = div_core(ua, ub, sgn, e0);
+  return a_zero ? dval(sgn) : q;
+}
+
+// RN(a / b) for all operands: the hardware instruction outside the fast domain.
+SFP_FN double div_rn(double a, double b) {
+  const uint64_t ua = dbits(a), ub = dbits(b);
+  const uint64_t sgn = (ua ^ ub) & kSign;
+  const uint32_t ea = (uint32_t)(ua >> 52) & 0x7ffu, eb = (uint32_t)(ub >> 52) & 0x7ffu;
+  const int e0 = (int)ea - (int)eb + 1023;
+  const bool b_normal = eb - 1u < 2046u;
+  if ((ua & kAbs) == 0 && b_normal) return dval(sgn);          // +-0 / normal
+  if (!(ea - 1u < 2046u && b_normal && (unsigned)(e0 - 2) < 2044u)) return hw_div(a, b);
+  return div_core(ua, ub, sgn, e0);
+}
+
+// RN(sqrt(x)) for x = dval(ux) positive and normal: three integer digits.
+SFP_FN double sqrt_core(uint64_t ux) {
+  const uint32_t ex = (uint32_t)(ux >> 52);
   const uint64_t mx = (ux & kFrac) | kImpl;
   const int E = (int)ex - 1023;
   const int odd = E & 1;
@@ -253,6 +272,21 @@ SFP_FN double sqrt_rn(double x) {
   // round to nearest (a square root is never half way): up iff R > S
   S += (R > (int64_t)S) ? 1 : 0;
   return dval(((uint64_t)(er - 1) << 52) + S);
+}
+
+// RN(sqrt(x)) for positive normal x, without a branch; for any other x (+-0,
+// subnormal, negative, inf, NaN) the result is unspecified and bad is set.
+SFP_FN double sqrt_fast(double x, unsigned &bad) {
+  const uint64_t ux = dbits(x);
+  bad |= ((uint32_t)(ux >> 52) - 1u < 2046u) ? 0u : 1u;   // the exponent field includes the sign
+  return sqrt_core(ux);
+}
+
+// RN(sqrt(x)) for all x: the hardware instruction outside the fast domain.
+SFP_FN double sqrt_rn(double x) {
+  const uint64_t ux = dbits(x);
+  if (!((uint32_t)(ux >> 52) - 1u < 2046u)) return hw_sqrt(x);   // +-0, subnormal, negative, inf, NaN
+  return sqrt_core(ux);
 }
 
 }  // namespace sfp

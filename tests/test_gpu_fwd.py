@@ -168,6 +168,39 @@ def test_zero_length_is_noop():
 
 # ------------------------------------------------------ full-size, sampled
 
+def sprinkled(n, rows, dtype, seed, every=997):
+    """N(0,1) batch with an edge matrix (zeros, subnormals, the top of the
+    exponent range, pivot ties) at every `every`-th position from 3: the
+    matrices the fast single-precision arithmetic hands to the fix-up pass,
+    scattered over blocks, vector lanes and the ragged tail."""
+    A = inputs.normal_batch(n, rows, seed, dtype)
+    E = inputs.edge_real(dtype)
+    m = E.shape[1]
+    idx = np.arange(3, n, every)
+    k = np.arange(len(idx))
+    if rows == 4:
+        A[:, idx] = E[:, k % m]
+    else:   # complex: real parts from one edge case, imaginary parts from another
+        A[0::2, idx] = E[:, k % m]
+        A[1::2, idx] = E[:, (k + 5) % m]
+    return np.ascontiguousarray(A)
+
+
+@pytest.mark.parametrize("rows", [4, 8])
+@pytest.mark.parametrize("backscale", [False, True])
+def test_fp32_fixup_pass_scattered_edges(rows, backscale):
+    """The FP32 kernels finish ordinary matrices on branch-free fast forms and
+    leave the rest (s = INT32_MIN) to a second pass with the general
+    arithmetic: the combined result must equal the oracle bit for bit, and no
+    sentinel may remain."""
+    A = sprinkled(2**18 + 5, rows, np.float32, 71 + rows)
+    g = gpu_svd2(A, backscale=backscale)
+    with np.errstate(all="ignore"):
+        o = oracle.svd2(A, backscale=backscale)
+    assert_same(g, o, f"fixup rows={rows} bs={backscale}")
+    assert not np.isin(g["s"], [np.iinfo(np.int32).min, np.iinfo(np.int32).min + 1]).any()
+
+
 def _sampled_check(A, what, nsample=1 << 15, seed=0):
     g = S.svd2(torch.from_numpy(A).cuda())
     torch.cuda.synchronize()

@@ -10,7 +10,7 @@ import oracle
 from paper_2005_07403_gb300 import inputs
 from paper_2005_07403_gb300 import svd2 as S
 from tests.helpers import bits_equal
-from tests.test_gpu_fwd import assert_same
+from tests.test_gpu_fwd import assert_same, sprinkled
 
 pytestmark = pytest.mark.gpu
 
@@ -88,3 +88,19 @@ def test_rerun_stated_error_full_size_sampled():
     assert en[~keep].max() <= 1.001 * u
     frac = cnt / A32.shape[1]
     assert 0.09 < frac < 0.12, frac
+
+
+@pytest.mark.parametrize("rows", [4, 8])
+def test_rerun_fixup_pass_scattered_edges(rows):
+    """Edge matrices among ordinary ones: those the fast single-precision pass
+    flags are finished by the fix-up pass (general single-precision method,
+    then the re-run test and the double re-run); results, s and the re-run
+    count equal the oracle's."""
+    A = sprinkled(2**17 + 9, rows, np.float32, 81 + rows, every=499)
+    for bs in (False, True):
+        g, cnt = run(A, -8, backscale=bs)
+        with np.errstate(all="ignore"):
+            o = oracle.svd2_rerun(A, -8, backscale=bs)
+        assert_same(g, o, f"rerun fixup rows={rows} bs={bs}")
+        assert cnt == o["count"]
+        assert not np.isin(g["s"], [np.iinfo(np.int32).min, np.iinfo(np.int32).min + 1]).any()
