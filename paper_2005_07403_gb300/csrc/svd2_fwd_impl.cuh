@@ -49,6 +49,16 @@ __device__ __forceinline__ void backscale(T &smax, T &smin, int32_t &s) {
   }
   s = 0;
 }
+// The same with the policy's scaling (FastAr flags results that leave the
+// normal range; the fix-up pass then back-scales them exactly).
+template <typename T, typename Ar>
+__device__ __forceinline__ void backscale(Ar &ar, T &smax, T &smin, int32_t &s) {
+  if (s != kZeroS) {
+    smax = ar.scale(smax, -s);
+    smin = ar.scale(smin, -s);
+  }
+  s = 0;
+}
 
 // One matrix with the given arithmetic policy (Sec. 2 - Sec. 7, Eq. 29).
 template <typename T, bool CPLX, typename Ar>
@@ -110,7 +120,7 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
     HotAr<T> ar;
     svd2_one<T, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
-    if (p.flags & SVD2_BACKSCALE) backscale(sx[m], sn[m], so[m]);
+    if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
     so[m] = ar.bad ? kRedoS : so[m];
     bad |= ar.bad;
 #pragma unroll
@@ -152,7 +162,8 @@ inline unsigned fix_grid(int64_t n) {
 
 // Minimum resident 512-thread blocks per SM the compiler must allow for: the
 // complex FP64 kernel is bound by arithmetic latency and runs best at 64
-// registers (32 warps per SM at 256 threads); the others may use up to 128.
+// registers (32 warps per SM); the others may use up to 128 (capping the FP32
+// kernels at 32 registers for full occupancy measured no faster).
 template <typename T, bool CPLX> constexpr int kMinBlocks = (sizeof(T) == 8 && CPLX) ? 2 : 1;
 
 template <typename T, bool CPLX, int M, int UNR>

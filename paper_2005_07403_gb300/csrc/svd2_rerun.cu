@@ -42,9 +42,15 @@ __device__ __forceinline__ int32_t rerun_one(Ar &ar, const FwdArgs<float, CPLX ?
   double u[NA], v[NA], sx, sn;
   int32_t s64;
   svd2_one<double, CPLX>(ar, ad, u, v, sx, sn, s64);
-  float fx = __double2float_rn(scalef(sx, s32 - s64));
-  float fn = __double2float_rn(scalef(sn, s32 - s64));
-  if (p.flags & SVD2_BACKSCALE) backscale(fx, fn, s32);
+  float fx = __double2float_rn(ar.scale(sx, s32 - s64));
+  float fn = __double2float_rn(ar.scale(sn, s32 - s64));
+  if (p.flags & SVD2_BACKSCALE) {
+    if (s32 != kZeroS) {
+      fx = ar.template scale_as<float>(fx, -s32);
+      fn = ar.template scale_as<float>(fn, -s32);
+    }
+    s32 = 0;
+  }
 #pragma unroll
   for (int e = 0; e < NA; ++e) {
     p.u[e][k] = __double2float_rn(u[e]);
@@ -85,7 +91,7 @@ __device__ __forceinline__ void fp32_group(const FwdArgs<float, CPLX ? 8 : 4> &p
     svd2_one<float, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
     if (!ar.bad && sn[m] < fp<float>::mul(p.tau, sx[m]))
       enqueue<NA>((uint32_t)(k0 + m), a, q_idx, q_a, qcap, q_n);
-    if (p.flags & SVD2_BACKSCALE) backscale(sx[m], sn[m], so[m]);
+    if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
     so[m] = ar.bad ? kRedoS : so[m];
     bad |= ar.bad;
 #pragma unroll
