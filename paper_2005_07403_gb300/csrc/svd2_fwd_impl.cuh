@@ -118,7 +118,7 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
     T a[NA], u[NA], v[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
-    HotAr<T> ar;
+    HotAr<T, CPLX> ar;
     svd2_one<T, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
     if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
     so[m] = ar.bad ? kRedoS : so[m];

@@ -63,7 +63,7 @@ __device__ __forceinline__ void multi_one(const MultiBatch &b, int64_t k, const 
   constexpr int NA = CPLX ? 8 : 4;
   double u[NA], v[NA], sx, sn;
   int32_t s;
-  HotAr<double> ar;
+  HotAr<double, CPLX> ar;
   svd2_one<double, CPLX>(ar, a, u, v, sx, sn, s);
   if (b.flags & SVD2_BACKSCALE) backscale(sx, sn, s);
   bad |= ar.bad;

@@ -87,7 +87,7 @@ __device__ __forceinline__ void fp32_group(const FwdArgs<float, CPLX ? 8 : 4> &p
     float a[NA], u[NA], v[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
-    FastAr<float> ar;
+    HotAr<float, CPLX> ar;
     svd2_one<float, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
     if (!ar.bad && sn[m] < fp<float>::mul(p.tau, sx[m]))
       enqueue<NA>((uint32_t)(k0 + m), a, q_idx, q_a, qcap, q_n);

@@ -201,6 +201,45 @@ def test_fp32_fixup_pass_scattered_edges(rows, backscale):
     assert not np.isin(g["s"], [np.iinfo(np.int32).min, np.iinfo(np.int32).min + 1]).any()
 
 
+def spread_cases(seed, spreads):
+    """Real FP32 matrices whose nonzero entries span a given number of binades:
+    the largest entry near 2^E (E = max(0, d - 120), so every entry stays
+    normal), others 2^(E-d) times a random significand, placed in every
+    position, with random signs; plus nearly and exactly singular ones
+    (a22 = a21 a12 / a11 up to a few ulps) whose r''22 (Eq. 7) cancels."""
+    rng = np.random.default_rng(seed)
+    cols = []
+    for d in spreads:
+        first = len(cols)
+        for pos in range(4):
+            for _ in range(24):
+                sig = rng.uniform(1.0, 2.0, 4) * rng.choice([-1.0, 1.0], 4)
+                e = -rng.integers(0, d + 1, 4)
+                e[pos] = -d
+                e[rng.integers(0, 4)] = 0
+                cols.append(np.ldexp(sig, e))
+        for _ in range(24):
+            a11, a21, a12 = np.ldexp(rng.uniform(1, 2, 3), [0, -d // 2, -(d - d // 2)])
+            for k in range(-2, 3):
+                a22 = np.float32(a21 * a12 / a11)
+                a22 = np.nextafter(a22, np.float32(np.inf)) if k > 0 else a22
+                cols.append([a11, a21, a12, a22 * (1 + k * 2.0**-23)])
+        E = max(0, d - 120)
+        cols[first:] = [np.ldexp(np.asarray(c, dtype=np.float64), E) for c in cols[first:]]
+    return np.ascontiguousarray(np.array(cols, dtype=np.float64).T.astype(np.float32))
+
+
+def test_fp32_spread_boundary_of_the_fast_path():
+    """The real FP32 kernels run the method at the scale h - 64 when every
+    nonzero entry is within 64 binades of the largest (and none is subnormal),
+    and hand the rest to the fix-up pass.  Matrices with spreads around that
+    boundary, and around the range where a shifted exponent would wrap, must
+    all match the oracle bit for bit."""
+    A = spread_cases(91, list(range(58, 71)) + list(range(180, 196)))
+    for bs in (False, True):
+        check(A, f"spread boundary bs={bs}", backscale=bs)
+
+
 def _sampled_check(A, what, nsample=1 << 15, seed=0):
     g = S.svd2(torch.from_numpy(A).cuda())
     torch.cuda.synchronize()
