@@ -386,6 +386,47 @@ def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
     return out
 
 
+def bench_variants(torch, S, stream, steps=10, warmup=3):
+    """The singular-values-only forms and the interleaved (n, 2, 2) layout on
+    the bench's two main shapes: complex128 n = 2^24 and real FP32 n = 2^26,
+    N(0,1) entries drawn on the device.  Per form: matrices/s, algorithmic
+    bytes per matrix and the fraction of the measured HBM copy bandwidth
+    (complex128: also of the FP64 pipe, with the method's FP64 add/mul/fma)."""
+    from paper_2005_07403_gb300 import inputs
+    peak, _ = measured_peaks()
+    fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3
+    out = {}
+    for name, rows, n, dt, cdt in (("complex128", 8, 2**24, torch.float64, torch.complex128),
+                                   ("real_fp32", 4, 2**26, torch.float32, torch.float32)):
+        A = inputs.normal_batch_device(n, rows, 131, "cuda", dt)
+        if rows == 8:   # (n, 2, 2) complex from the split rows (Re, Im of a11, a21, a12, a22)
+            el = [torch.complex(A[2 * e], A[2 * e + 1]) for e in range(4)]
+        else:
+            el = [A[e] for e in range(4)]
+        M = torch.stack([el[0], el[2], el[1], el[3]], dim=1).reshape(n, 2, 2).to(cdt).contiguous()
+        res = {}
+        vals = S.svd2_values(A)
+        es = torch.finfo(dt).bits // 8
+        b_vals = rows * es + 2 * es + 4
+        b_full = 3 * rows * es + 2 * es + 4
+        for form, fn, bpm in (
+                ("values_only", lambda: S.svd2_values(A, out=vals), b_vals),
+                ("interleaved", lambda: S.svd2_interleaved(M), b_full),
+                ("interleaved_values_only", lambda: S.svd2_interleaved(M, values_only=True), b_vals)):
+            ms = time_steps(torch, fn, steps, warmup, stream)
+            r = {"matrices_per_s": n / (ms / 1e3), "ms": ms, "bytes_per_matrix": bpm,
+                 "hbm_frac": bpm * n / (ms / 1e3) / 1e9 / peak}
+            res[form] = r
+        if rows == 8:
+            # the values-only complex method skips Eq. 29: 53 of its 91 FP64 operations remain
+            res["values_only"]["fp64_pipe_frac"] = 53 * n / (res["values_only"]["ms"] / 1e3) / 1e9 / fp64_peak
+            res["interleaved"]["fp64_pipe_frac"] = 91 * n / (res["interleaved"]["ms"] / 1e3) / 1e9 / fp64_peak
+        out[name] = dict(n=n, **res)
+        del A, M, vals
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2005_07403_gb300 import svd2 as S
@@ -506,6 +547,7 @@ def run_ours(args):
                                                  args.warmup, stream)
         line["multi_batch"] = bench_multi(torch, S, stream)
         line["differentiation"] = bench_grad(torch, S, stream)
+        line["variants"] = bench_variants(torch, S, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, W["rows"])
     if dist is not None:

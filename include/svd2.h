@@ -95,6 +95,44 @@ int svd2_batch_c(int64_t n, const float *const A[8], float *const U[8],
                  uint32_t flags, svd2_stream_t stream);
 
 /*
+ * Singular values only (the counterpart of LAPACK's xLAS2, named with xLASV2
+ * at the start of Sec. 2): the method of svd2_batch_{d,z,s,c} without the
+ * assembly of U and V (Eq. 28, Eq. 29) and without their stores.  smax, smin
+ * and s receive exactly the values the full form stores (Sigma', s; with
+ * SVD2_BACKSCALE, Sigma and s = 0).  A as for the full form; the per-matrix
+ * traffic falls to 52 B (real FP64), 84 B (complex128), 28 B (real FP32),
+ * 44 B (complex64).  Errors as above.
+ */
+int svd2_values_d(int64_t n, const double *const A[4], double *smax, double *smin,
+                  int32_t *s, uint32_t flags, svd2_stream_t stream);
+int svd2_values_z(int64_t n, const double *const A[8], double *smax, double *smin,
+                  int32_t *s, uint32_t flags, svd2_stream_t stream);
+int svd2_values_s(int64_t n, const float *const A[4], float *smax, float *smin,
+                  int32_t *s, uint32_t flags, svd2_stream_t stream);
+int svd2_values_c(int64_t n, const float *const A[8], float *smax, float *smin,
+                  int32_t *s, uint32_t flags, svd2_stream_t stream);
+
+/*
+ * The interleaved layout: the n matrices as one row-major (n, 2, 2) array, each
+ * matrix's entries contiguous -- the one-matrix-at-a-time data of the
+ * pointwise routine x1svd2 (Sec. 4: the interface of Sec. 4 with S = 1), and
+ * torch's layout for a batch of 2x2 real or complex matrices.  A, U, V: device pointers to n*4 values (real: a11 a12 a21
+ * a22) or n*8 values (complex: Re a11, Im a11, Re a12, Im a12, Re a21, Im a21,
+ * Re a22, Im a22); U and V in the same layout.  U and V both NULL: singular
+ * values only; one NULL: SVD2_EINVAL.  smax, smin, s: n values each.  Results
+ * bit-identical to the split-layout forms on the same matrices.  Errors as
+ * above.
+ */
+int svd2_batch_interleaved_d(int64_t n, const double *A, double *U, double *V, double *smax,
+                             double *smin, int32_t *s, uint32_t flags, svd2_stream_t stream);
+int svd2_batch_interleaved_z(int64_t n, const double *A, double *U, double *V, double *smax,
+                             double *smin, int32_t *s, uint32_t flags, svd2_stream_t stream);
+int svd2_batch_interleaved_s(int64_t n, const float *A, float *U, float *V, float *smax,
+                             float *smin, int32_t *s, uint32_t flags, svd2_stream_t stream);
+int svd2_batch_interleaved_c(int64_t n, const float *A, float *U, float *V, float *smax,
+                             float *smin, int32_t *s, uint32_t flags, svd2_stream_t stream);
+
+/*
  * FP32 form with FP64 re-run.  The single-precision method (as svd2_batch_s /
  * svd2_batch_c) runs over all n matrices; every matrix whose scaled singular
  * values satisfy sigma'_min < 2^tau_log2 * sigma'_max (compared in float, the

@@ -30,6 +30,10 @@ struct FwdArgs {
   unsigned long long *count;
   // Set to nonzero by the fast kernel when it flagged a matrix (see fix_kernel).
   unsigned long long *redo;
+  // Elements between consecutive matrices in every array of A, U and V: 1 for
+  // the split layout, 4 or 8 for the interleaved (n, 2, 2) layout, where each
+  // pointer addresses one element of the first matrix.  smax, smin, s: 1.
+  int64_t stride;
 };
 
 // s written by the fast kernel for a matrix it could not finish: its outputs
@@ -79,23 +83,25 @@ template <typename T> struct SigmaPair {
 // stored over whatever the fast kernel stored for it; returns sigma'_max and
 // sigma'_min before any back-scaling.  The element arrays may live in any
 // address space.
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, bool VALS = false>
 __device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u, T *const *v,
-                                               T *smax, T *smin, int32_t *s, uint32_t flags,
-                                               int64_t k) {
+                                                  T *smax, T *smin, int32_t *s, uint32_t flags,
+                                                  int64_t k, int64_t stride = 1) {
   constexpr int NA = CPLX ? 8 : 4;
   T ai[NA], uo[NA], vo[NA], sx, sn;
   int32_t so;
 #pragma unroll
-  for (int e = 0; e < NA; ++e) ai[e] = a[e][k];
+  for (int e = 0; e < NA; ++e) ai[e] = a[e][k * stride];
   ExactAr<T> ar;
   svd2_one<T, CPLX>(ar, ai, uo, vo, sx, sn, so);
   const SigmaPair<T> r{sx, sn};
   if (flags & SVD2_BACKSCALE) backscale(sx, sn, so);
+  if constexpr (!VALS) {
 #pragma unroll
-  for (int e = 0; e < NA; ++e) {
-    u[e][k] = uo[e];
-    v[e][k] = vo[e];
+    for (int e = 0; e < NA; ++e) {
+      u[e][k * stride] = uo[e];
+      v[e][k * stride] = vo[e];
+    }
   }
   smax[k] = sx;
   smin[k] = sn;
@@ -106,7 +112,7 @@ __device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u
 // M matrices from k0 with the batch arithmetic HotAr, stored with vector
 // stores; a matrix the fast arithmetic cannot finish gets s = kRedoS and
 // raises p.redo.
-template <typename T, bool CPLX, int M>
+template <typename T, bool CPLX, int M, bool VALS = false>
 __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p, int64_t k0,
                                               const T (&in)[CPLX ? 8 : 4][M]) {
   constexpr int NA = CPLX ? 8 : 4;
@@ -129,10 +135,12 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
       vo[e][m] = v[e];
     }
   }
+  if constexpr (!VALS) {
 #pragma unroll
-  for (int e = 0; e < NA; ++e) store_vec<T, M>(p.u[e] + k0, uo[e]);
+    for (int e = 0; e < NA; ++e) store_vec<T, M>(p.u[e] + k0, uo[e]);
 #pragma unroll
-  for (int e = 0; e < NA; ++e) store_vec<T, M>(p.v[e] + k0, vo[e]);
+    for (int e = 0; e < NA; ++e) store_vec<T, M>(p.v[e] + k0, vo[e]);
+  }
   store_vec<T, M>(p.smax + k0, sx);
   store_vec<T, M>(p.smin + k0, sn);
   store_vec<int32_t, M>(p.s + k0, so);
@@ -145,12 +153,13 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
 // divisor or scaled entry, or an exponent out of the fast range: zero columns,
 // zero matrices, entries spanning more than the exponent range.  Otherwise the
 // pass reads one word and ends.
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, bool VALS>
 __global__ void __launch_bounds__(256) fix_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
   if (*p.redo == 0) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride)
-    if (p.s[k] == kRedoS) exact_one<T, CPLX>(p.a, p.u, p.v, p.smax, p.smin, p.s, p.flags, k);
+    if (p.s[k] == kRedoS)
+      exact_one<T, CPLX, VALS>(p.a, p.u, p.v, p.smax, p.smin, p.s, p.flags, k, p.stride);
 }
 
 // Blocks of the fix-up pass: enough to scan a batch quickly when it has work.
@@ -161,12 +170,12 @@ inline unsigned fix_grid(int64_t n) {
 }
 
 // Minimum resident 512-thread blocks per SM the compiler must allow for: the
-// complex FP64 kernel is bound by arithmetic latency and runs best at 64
-// registers (32 warps per SM); the others may use up to 128 (capping the FP32
-// kernels at 32 registers for full occupancy measured no faster).
-template <typename T, bool CPLX> constexpr int kMinBlocks = (sizeof(T) == 8 && CPLX) ? 2 : 1;
+// FP64 kernels are bound by arithmetic latency and run best at 64 registers
+// (32 warps per SM); the FP32 ones may use up to 128 (capping them at 32
+// registers for full occupancy measured no faster).
+template <typename T, bool CPLX> constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 1;
 
-template <typename T, bool CPLX, int M, int UNR>
+template <typename T, bool CPLX, int M, int UNR, bool VALS = false>
 __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
     fwd_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
       const int64_t g = g0 + r * stride;
-      if (g < ngroups) process_group<T, CPLX, M>(p, g * M, in[r]);
+      if (g < ngroups) process_group<T, CPLX, M, VALS>(p, g * M, in[r]);
     }
   }
   // the n mod M tail, one matrix per thread
@@ -195,58 +204,136 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
     T in1[NA][1];
 #pragma unroll
     for (int e = 0; e < NA; ++e) in1[e][0] = p.a[e][k];
-    process_group<T, CPLX, 1>(p, k, in1);
+    process_group<T, CPLX, 1, VALS>(p, k, in1);
+  }
+}
+
+// The interleaved layout (p.stride == NA, each matrix one contiguous record):
+// one matrix per thread.  REC: the record is moved with 16-byte vector loads
+// and stores (every base pointer 16-byte aligned; a record is 16, 32 or 64
+// bytes) and permuted to the record order of Sec. 8 in registers; otherwise
+// element loads and stores at the layout's stride.
+template <bool CPLX> constexpr int interleaved_offset(int e);
+
+template <typename T, bool CPLX, bool VALS, bool REC>
+__global__ void __launch_bounds__(256, 2 * kMinBlocks<T, CPLX>) strided_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
+  constexpr int NA = CPLX ? 8 : 4;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += step) {
+    T a[NA], u[NA], v[NA], sx, sn;
+    int32_t so;
+    if constexpr (REC) {
+      T rec[NA];
+      load_vec<T, NA>(p.a[0] + k * NA, rec);
+#pragma unroll
+      for (int e = 0; e < NA; ++e) a[e] = rec[interleaved_offset<CPLX>(e)];
+    } else {
+#pragma unroll
+      for (int e = 0; e < NA; ++e) a[e] = __ldcs(p.a[e] + k * p.stride);
+    }
+    HotAr<T, CPLX> ar;
+    svd2_one<T, CPLX>(ar, a, u, v, sx, sn, so);
+    if (p.flags & SVD2_BACKSCALE) backscale(ar, sx, sn, so);
+    if constexpr (!VALS) {
+      if constexpr (REC) {
+        T ru[NA], rv[NA];
+#pragma unroll
+        for (int e = 0; e < NA; ++e) {
+          ru[interleaved_offset<CPLX>(e)] = u[e];
+          rv[interleaved_offset<CPLX>(e)] = v[e];
+        }
+        store_vec<T, NA>(p.u[0] + k * NA, ru);
+        store_vec<T, NA>(p.v[0] + k * NA, rv);
+      } else {
+#pragma unroll
+        for (int e = 0; e < NA; ++e) {
+          __stcs(p.u[e] + k * p.stride, u[e]);
+          __stcs(p.v[e] + k * p.stride, v[e]);
+        }
+      }
+    }
+    __stcs(p.smax + k, sx);
+    __stcs(p.smin + k, sn);
+    __stcs(p.s + k, ar.bad ? kRedoS : so);
+    if (ar.bad) *p.redo = 1;
   }
 }
 
 template <typename T, bool CPLX>
 using FwdKernel = void (*)(const FwdArgs<T, CPLX ? 8 : 4>);
 
+// The values-only kernels exist for one load group in flight only.
 template <typename T, bool CPLX>
-inline FwdKernel<T, CPLX> pick_kernel(int mpt, int unroll) {
+inline FwdKernel<T, CPLX> pick_kernel(int mpt, int unroll, bool vals) {
 #define SVD2_PICK(M_, U_) \
-  if (mpt == M_ && unroll == U_) return fwd_kernel<T, CPLX, M_, U_>;
-  SVD2_PICK(1, 1) SVD2_PICK(1, 2) SVD2_PICK(2, 1) SVD2_PICK(2, 2) SVD2_PICK(4, 1) SVD2_PICK(4, 2)
+  if (mpt == M_ && unroll == U_) return fwd_kernel<T, CPLX, M_, U_, false>;
+  if (!vals) {
+    SVD2_PICK(1, 1) SVD2_PICK(1, 2) SVD2_PICK(2, 1) SVD2_PICK(2, 2) SVD2_PICK(4, 1) SVD2_PICK(4, 2)
+    return nullptr;
+  }
 #undef SVD2_PICK
+  if (mpt == 1) return fwd_kernel<T, CPLX, 1, 1, true>;
+  if (mpt == 2) return fwd_kernel<T, CPLX, 2, 1, true>;
+  if (mpt == 4) return fwd_kernel<T, CPLX, 4, 1, true>;
   return nullptr;
 }
 
 // Validate the arguments, fill p and launch the forward kernel for op on n
-// matrices.  Returns an SVD2_* code.
+// matrices.  vals: singular values only (U, V neither computed nor stored,
+// Uo and Vo may be NULL).  stride: elements between consecutive matrices in
+// the arrays of A, U and V (1: split layout).  Returns an SVD2_* code.
 template <typename T, bool CPLX>
 inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *const *Vo, T *smax,
                       T *smin, int32_t *s, uint32_t flags, cudaStream_t stream,
-                      FwdArgs<T, CPLX ? 8 : 4> &p) {
+                      FwdArgs<T, CPLX ? 8 : 4> &p, bool vals = false, int64_t stride = 1) {
   constexpr int NA = CPLX ? 8 : 4;
-  if (n < 0 || (flags & ~SVD2_BACKSCALE)) return SVD2_EINVAL;
+  if (n < 0 || stride < 1 || (flags & ~SVD2_BACKSCALE)) return SVD2_EINVAL;
   if (n == 0) return SVD2_OK;
-  if (!A || !Uo || !Vo || !smax || !smin || !s) return SVD2_EINVAL;
-  bool vec_ok = aligned(smax, 16) && aligned(smin, 16) && aligned(s, 16);
+  if (!A || (!vals && (!Uo || !Vo)) || !smax || !smin || !s) return SVD2_EINVAL;
+  bool vec_ok = stride == 1 && aligned(smax, 16) && aligned(smin, 16) && aligned(s, 16);
   for (int e = 0; e < NA; ++e) {
-    if (!A[e] || !Uo[e] || !Vo[e]) return SVD2_EINVAL;
+    if (!A[e] || (!vals && (!Uo[e] || !Vo[e]))) return SVD2_EINVAL;
     p.a[e] = A[e];
-    p.u[e] = Uo[e];
-    p.v[e] = Vo[e];
-    vec_ok = vec_ok && aligned(A[e], 16) && aligned(Uo[e], 16) && aligned(Vo[e], 16);
+    p.u[e] = vals ? nullptr : Uo[e];
+    p.v[e] = vals ? nullptr : Vo[e];
+    vec_ok = vec_ok && aligned(A[e], 16) && (vals || (aligned(Uo[e], 16) && aligned(Vo[e], 16)));
   }
   p.smax = smax;
   p.smin = smin;
   p.s = s;
   p.n = n;
   p.flags = flags;
-  Launch L = get_launch(op);
-  if (!vec_ok) L.mpt = 1;
-  FwdKernel<T, CPLX> k = pick_kernel<T, CPLX>(L.mpt, L.unroll);
-  if (!k) return SVD2_EINVAL;
-  int resident = 0;
-  SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, L.block, 0));
-  const int64_t groups = n / L.mpt;
-  const int64_t tail = n % L.mpt;
-  const int64_t loops = (groups + L.unroll - 1) / L.unroll;
-  const int64_t units = loops > tail ? loops : tail;   // threads needed
-  const int64_t grid = grid_for(units, L, resident);
+  p.stride = stride;
+  FwdKernel<T, CPLX> k = nullptr;
+  int64_t grid = 0;
+  unsigned block = 256;
+  if (stride > 1) {
+    // whole records when the layout is the interleaved one and every base is aligned
+    const bool rec = stride == NA && aligned(A[0], 16) &&
+                     (vals || (aligned(Uo[0], 16) && aligned(Vo[0], 16)));
+    if (rec)
+      k = vals ? strided_kernel<T, CPLX, true, true> : strided_kernel<T, CPLX, false, true>;
+    else
+      k = vals ? strided_kernel<T, CPLX, true, false> : strided_kernel<T, CPLX, false, false>;
+    const int64_t want = (n + 255) / 256;
+    grid = want < 0x7fffffffLL ? want : 0x7fffffffLL;
+  } else {
+    Launch L = get_launch(op);
+    if (!vec_ok) L.mpt = 1;
+    if (vals) L.unroll = 1;
+    k = pick_kernel<T, CPLX>(L.mpt, L.unroll, vals);
+    if (!k) return SVD2_EINVAL;
+    int resident = 0;
+    SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, L.block, 0));
+    const int64_t groups = n / L.mpt;
+    const int64_t tail = n % L.mpt;
+    const int64_t loops = (groups + L.unroll - 1) / L.unroll;
+    const int64_t units = loops > tail ? loops : tail;   // threads needed
+    grid = grid_for(units, L, resident);
+    block = (unsigned)L.block;
+  }
   if constexpr (!kHotFlags<T>) {
-    k<<<(unsigned)grid, L.block, 0, stream>>>(p);
+    k<<<(unsigned)grid, block, 0, stream>>>(p);
     SVD2_CUDA_TRY(cudaGetLastError());
     return SVD2_OK;
   } else {
@@ -254,16 +341,52 @@ inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *con
     int rc = flag_block(stream, &flag);
     if (rc != SVD2_OK) return rc;
     p.redo = static_cast<unsigned long long *>(flag);
-    k<<<(unsigned)grid, L.block, 0, stream>>>(p);
+    k<<<(unsigned)grid, block, 0, stream>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-      fix_kernel<T, CPLX><<<fix_grid(n), 256, 0, stream>>>(p);
+      if (vals)
+        fix_kernel<T, CPLX, true><<<fix_grid(n), 256, 0, stream>>>(p);
+      else
+        fix_kernel<T, CPLX, false><<<fix_grid(n), 256, 0, stream>>>(p);
       e = cudaGetLastError();
     }
     rc = flag_release(flag, stream);
     if (e != cudaSuccess) return record_cuda_error(e);
     return rc;
   }
+}
+
+// The interleaved layout of a (n, 2, 2) row-major array (torch's layout for a
+// batch of 2x2 real or complex matrices): matrix k's entries are contiguous,
+// real: a11 a12 a21 a22; complex: Re a11, Im a11, Re a12, Im a12, Re a21,
+// Im a21, Re a22, Im a22.  Offset of the record-order element e (Sec. 8:
+// a11, a21, a12, a22, real and imaginary parts interleaved) in one matrix.
+template <bool CPLX> constexpr int interleaved_offset(int e) {
+  if (CPLX) {
+    const int elem = e >> 1, part = e & 1;             // elem: a11, a21, a12, a22
+    const int rm = (elem == 1) ? 2 : (elem == 2) ? 1 : elem;   // row-major position
+    return 2 * rm + part;
+  }
+  return (e == 1) ? 2 : (e == 2) ? 1 : e;
+}
+
+// launch_fwd on an interleaved batch at base pointers A, U, V.
+template <typename T, bool CPLX>
+inline int launch_interleaved(int op, int64_t n, const T *A, T *U, T *V, T *smax, T *smin,
+                              int32_t *s, uint32_t flags, cudaStream_t stream, bool vals) {
+  constexpr int NA = CPLX ? 8 : 4;
+  if (n < 0 || (flags & ~SVD2_BACKSCALE)) return SVD2_EINVAL;
+  if (n == 0) return SVD2_OK;
+  if (!A || (!vals && (!U || !V))) return SVD2_EINVAL;
+  const T *a[NA];
+  T *u[NA], *v[NA];
+  for (int e = 0; e < NA; ++e) {
+    a[e] = A + interleaved_offset<CPLX>(e);
+    u[e] = vals ? nullptr : U + interleaved_offset<CPLX>(e);
+    v[e] = vals ? nullptr : V + interleaved_offset<CPLX>(e);
+  }
+  FwdArgs<T, NA> p{};
+  return launch_fwd<T, CPLX>(op, n, a, u, v, smax, smin, s, flags, stream, p, vals, NA);
 }
 
 }  // namespace svd2

@@ -269,6 +269,7 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
     p.tau = ldexpf(1.0f, tau_log2);
     p.count = count;
     p.redo = count + 1;
+    p.stride = 1;
     const int64_t tiles = (m / L.mpt + (int64_t)L.block * L.unroll - 1) / ((int64_t)L.block * L.unroll);
     const int64_t cap = (int64_t)sm_count() * (resident > 0 ? resident : 1) * (L.waves > 0 ? L.waves : 1 << 20);
     int64_t grid = tiles < 1 ? 1 : tiles;

@@ -80,6 +80,15 @@ def _declare(L):
         f = getattr(L, name)
         f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_uint32, P]
         f.restype = ctypes.c_int
+    for name in ("svd2_values_d", "svd2_values_z", "svd2_values_s", "svd2_values_c"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_int64, PP, P, P, P, ctypes.c_uint32, P]
+        f.restype = ctypes.c_int
+    for name in ("svd2_batch_interleaved_d", "svd2_batch_interleaved_z",
+                 "svd2_batch_interleaved_s", "svd2_batch_interleaved_c"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_uint32, P]
+        f.restype = ctypes.c_int
     for name in ("svd2_batch_s_rerun", "svd2_batch_c_rerun"):
         f = getattr(L, name)
         f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int, ctypes.c_uint32, P,
@@ -200,6 +209,65 @@ def svd2(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = N
     rc = f(n, ptr_array(a_ptrs), ptr_array(u_ptrs), ptr_array(v_ptrs), out.smax.data_ptr(),
            out.smin.data_ptr(), out.s.data_ptr(), BACKSCALE if backscale else 0, h)
     check(rc, "svd2_batch_" + kind)
+    return out
+
+
+@dataclass
+class Svd2Values:
+    smax: torch.Tensor
+    smin: torch.Tensor
+    s: torch.Tensor
+
+
+def svd2_values(A: torch.Tensor, *, backscale: bool = False, out: Svd2Values | None = None,
+                stream: int | None = None) -> Svd2Values:
+    """Singular values only (svd2_values_*): the split-layout batch ``A`` as in
+    svd2(); returns sigma'_max, sigma'_min and s (sigma with s = 0 when
+    ``backscale``), the same values svd2() stores."""
+    rows, n = A.shape
+    kind = _kind(rows, A.dtype)
+    a_ptrs = _rows(A, "A")
+    if out is None:
+        out = Svd2Values(smax=torch.empty(n, dtype=A.dtype, device=A.device),
+                         smin=torch.empty(n, dtype=A.dtype, device=A.device),
+                         s=torch.empty(n, dtype=torch.int32, device=A.device))
+    h = current_stream_handle(A.device) if stream is None else stream
+    rc = getattr(lib(), "svd2_values_" + kind)(
+        n, ptr_array(a_ptrs), out.smax.data_ptr(), out.smin.data_ptr(), out.s.data_ptr(),
+        BACKSCALE if backscale else 0, h)
+    check(rc, "svd2_values_" + kind)
+    return out
+
+
+_INTERLEAVED_KIND = {torch.float64: "d", torch.complex128: "z", torch.float32: "s",
+                     torch.complex64: "c"}
+
+
+def svd2_interleaved(A: torch.Tensor, *, values_only: bool = False, backscale: bool = False,
+                     stream: int | None = None) -> Svd2Result:
+    """The interleaved layout (svd2_batch_interleaved_*): ``A`` of shape (n, 2, 2),
+    float64, float32, complex128 or complex64, contiguous, on a CUDA device.
+    Returns U, V of A's shape and dtype (None with ``values_only``), and
+    sigma'_max, sigma'_min (the real dtype) and s, so that
+    A = U diag(2^-s sigma') V^H; with ``backscale`` sigma and s = 0."""
+    if A.dim() != 3 or tuple(A.shape[1:]) != (2, 2) or not A.is_contiguous() or not A.is_cuda:
+        raise ValueError("A must be a contiguous CUDA tensor of shape (n, 2, 2)")
+    kind = _INTERLEAVED_KIND.get(A.dtype)
+    if kind is None:
+        raise TypeError(f"unsupported dtype {A.dtype}")
+    n = A.shape[0]
+    rdt = torch.float64 if kind in "dz" else torch.float32
+    out = Svd2Result(U=None if values_only else torch.empty_like(A),
+                     V=None if values_only else torch.empty_like(A),
+                     smax=torch.empty(n, dtype=rdt, device=A.device),
+                     smin=torch.empty(n, dtype=rdt, device=A.device),
+                     s=torch.empty(n, dtype=torch.int32, device=A.device))
+    h = current_stream_handle(A.device) if stream is None else stream
+    rc = getattr(lib(), "svd2_batch_interleaved_" + kind)(
+        n, A.data_ptr(), None if values_only else out.U.data_ptr(),
+        None if values_only else out.V.data_ptr(), out.smax.data_ptr(), out.smin.data_ptr(),
+        out.s.data_ptr(), BACKSCALE if backscale else 0, h)
+    check(rc, "svd2_batch_interleaved_" + kind)
     return out
 
 

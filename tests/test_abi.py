@@ -51,6 +51,17 @@ def test_invalid_arguments_rejected_on_host():
     # n == 0 is a no-op
     assert L.svd2_batch_z(0, None, None, None, None, None, None, 0, None) == S.OK
     assert L.svd2_batch_c(0, None, None, None, None, None, None, 0, None) == S.OK
+    # values only: same rules
+    assert L.svd2_values_d(-1, z, None, None, None, 0, None) == S.EINVAL
+    assert L.svd2_values_s(5, None, None, None, None, 0, None) == S.EINVAL
+    assert L.svd2_values_z(0, None, None, None, None, 0, None) == S.OK
+    # interleaved: exactly one of U, V NULL, unknown flags, n < 0 (no pointer is dereferenced)
+    fake = 256
+    assert L.svd2_batch_interleaved_d(5, fake, fake, None, fake, fake, fake, 0, None) == S.EINVAL
+    assert L.svd2_batch_interleaved_c(5, fake, None, fake, fake, fake, fake, 0, None) == S.EINVAL
+    assert L.svd2_batch_interleaved_z(0, None, None, None, None, None, None, 0x80, None) == S.EINVAL
+    assert L.svd2_batch_interleaved_s(-1, fake, fake, fake, fake, fake, fake, 0, None) == S.EINVAL
+    assert L.svd2_batch_interleaved_s(0, None, None, None, None, None, None, 0, None) == S.OK
 
 
 def test_launch_table_roundtrip_and_validation():
