@@ -427,6 +427,43 @@ def bench_variants(torch, S, stream, steps=10, warmup=3):
     return out
 
 
+def bench_kog(torch, S, stream, steps=10, warmup=3):
+    """One parallel Kogbetliantz step (Sec. 1) on m x m matrices of N(0,1)
+    entries drawn on the device: complex128 and real FP64 with m = 8192
+    (column-major), real FP32 with m = 16384; with the pivot pairs (2i, 2i+1)
+    (contiguous 2x2 blocks) and with one round-robin step (gathered rows and
+    columns).  G is updated in place every step (the transformation is
+    unitary, so the values stay bounded).  Per case: steps/s, the update's
+    algorithmic bytes (G read and written once) against the HBM copy peak and,
+    in FP64, its operations (64 per complex 2x2 block, 16 per real one)
+    against the FP64 pipe."""
+    from paper_2005_07403_gb300 import inputs
+    peak, _ = measured_peaks()
+    fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3
+    out = {}
+    for name, m, dt, ops in (("complex128", 8192, torch.complex128, 64),
+                             ("real_fp64", 8192, torch.float64, 16),
+                             ("real_fp32", 16384, torch.float32, 16)):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(141)
+        G = torch.randn((m, m), generator=g, device="cuda", dtype=dt).T   # column-major
+        ws = S.kog_workspace(G)
+        res = {"m": m}
+        for order, pairs in (("adjacent", torch.arange(m, dtype=torch.int32, device="cuda")),
+                             ("round_robin", torch.from_numpy(inputs.round_robin_pairs(m, 1)).cuda())):
+            ms = time_steps(torch, lambda: S.kog_step(G, pairs, workspace=ws), steps, warmup, stream)
+            nbytes = 2 * m * m * G.element_size()
+            r = {"steps_per_s": 1e3 / ms, "ms": ms, "bytes_per_step": nbytes,
+                 "hbm_frac": nbytes / (ms / 1e3) / 1e9 / peak}
+            if dt != torch.float32:
+                r["fp64_pipe_frac"] = ops * (m // 2) ** 2 / (ms / 1e3) / 1e9 / fp64_peak
+            res[order] = r
+        out[name] = res
+        del G, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2005_07403_gb300 import svd2 as S
@@ -548,6 +585,7 @@ def run_ours(args):
         line["multi_batch"] = bench_multi(torch, S, stream)
         line["differentiation"] = bench_grad(torch, S, stream)
         line["variants"] = bench_variants(torch, S, stream)
+        line["kogbetliantz_step"] = bench_kog(torch, S, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, W["rows"])
     if dist is not None:

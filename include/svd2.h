@@ -133,6 +133,40 @@ int svd2_batch_interleaved_c(int64_t n, const float *A, float *U, float *V, floa
                              float *smin, int32_t *s, uint32_t flags, svd2_stream_t stream);
 
 /*
+ * One parallel step of the Kogbetliantz method for the SVD of an m x m matrix
+ * G (Sec. 1), m = 2n even.  pairs: device array of m int32, the pivot pairs
+ * (p_0, q_0, p_1, q_1, ...), together a permutation of 0 .. m-1.  The step
+ * gathers the n pivot blocks A^[k] (elements (p_k,p_k), (q_k,p_k), (p_k,q_k),
+ * (q_k,q_k)), computes their SVDs by the method (with the back-scaling of
+ * Fig. 1), and updates G in place from the left by (U^[k])^* on rows p_k, q_k
+ * and from the right by V^[k] on columns p_k, q_k; the pivot blocks become
+ * diag(sigma_max, sigma_min) with the off-diagonal pivot positions exactly 0.
+ * G: device matrix, element (r, c) at G[r rs + c cs] -- column-major
+ * (rs = 1, cs = leading dimension >= m) or row-major (cs = 1, rs >= m); for
+ * z and c the elements are complex (real and imaginary part adjacent, as in
+ * complex128/complex64 arrays), strides counted in complex elements.
+ * workspace: device memory of svd2_kog_workspace_bytes(op, m) bytes (op:
+ * 0 = d, 1 = z, 2 = s, 3 = c), 256-byte aligned, used by this call only; it
+ * holds U, V, Sigma of the step and, at offset 0, the number of pairs skipped
+ * because an index was outside 0 .. m-1 or p = q (svd2_kog_skipped; every
+ * 2x2 block in the rows or the columns of a skipped pair is left untouched).  Pairs that repeat an index give
+ * unspecified values (the blocks overlap) but never an out-of-range access.
+ * Two kernels on `stream`.  Errors: SVD2_EINVAL for m odd or < 2, NULL
+ * pointers, another layout, a small or misaligned workspace; SVD2_ECUDA.
+ */
+size_t svd2_kog_workspace_bytes(int op, int64_t m);
+int svd2_kog_step_d(int64_t m, double *G, int64_t rs, int64_t cs, const int32_t *pairs,
+                    void *workspace, size_t workspace_bytes, svd2_stream_t stream);
+int svd2_kog_step_z(int64_t m, double *G, int64_t rs, int64_t cs, const int32_t *pairs,
+                    void *workspace, size_t workspace_bytes, svd2_stream_t stream);
+int svd2_kog_step_s(int64_t m, float *G, int64_t rs, int64_t cs, const int32_t *pairs,
+                    void *workspace, size_t workspace_bytes, svd2_stream_t stream);
+int svd2_kog_step_c(int64_t m, float *G, int64_t rs, int64_t cs, const int32_t *pairs,
+                    void *workspace, size_t workspace_bytes, svd2_stream_t stream);
+/* Pairs skipped by the last step that used `workspace`; synchronous. */
+int svd2_kog_skipped(const void *workspace, int64_t *count);
+
+/*
  * FP32 form with FP64 re-run.  The single-precision method (as svd2_batch_s /
  * svd2_batch_c) runs over all n matrices; every matrix whose scaled singular
  * values satisfy sigma'_min < 2^tau_log2 * sigma'_max (compared in float, the

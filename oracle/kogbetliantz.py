@@ -101,21 +101,6 @@ def embedded_unitaries(m, pairs, U, V):
     return Uf, Vf
 
 
-def round_robin_pairs(m, step):
-    """Pivot pairs of step `step` (0 .. m-2) of the round-robin tournament
-    ordering: every index meets every other exactly once per m - 1 steps (a
-    cyclic parallel ordering; the paper leaves the choice open)."""
-    others = list(range(1, m))
-    r = step % (m - 1)
-    rot = others[r:] + others[:r]
-    players = [0] + rot
-    pairs = []
-    for i in range(m // 2):
-        a, b = players[i], players[m - 1 - i]
-        pairs += [min(a, b), max(a, b)]
-    return np.array(pairs, dtype=np.int32)
-
-
 def off_norm(G):
     """Frobenius norm of the off-diagonal part."""
     return float(np.linalg.norm(G - np.diag(np.diag(G))))

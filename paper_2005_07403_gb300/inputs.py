@@ -262,3 +262,19 @@ def normal_batch_device(n: int, rows: int, seed: int, device="cuda", dtype=None)
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     return torch.randn((rows, n), generator=g, device=device, dtype=dtype or torch.float64)
+
+
+def round_robin_pairs(m: int, step: int) -> np.ndarray:
+    """Pivot pairs (p_0, q_0, p_1, q_1, ...) of step `step` (0 .. m-2) of the
+    round-robin tournament ordering of 0 .. m-1 (m even): every index meets
+    every other exactly once in m - 1 steps, a cyclic parallel ordering for
+    the Kogbetliantz step of Sec. 1 (the paper leaves the ordering open).
+    int32 array of m entries, each pair with p < q."""
+    others = list(range(1, m))
+    r = step % (m - 1)
+    players = [0] + others[r:] + others[:r]
+    pairs = []
+    for i in range(m // 2):
+        a, b = players[i], players[m - 1 - i]
+        pairs += [min(a, b), max(a, b)]
+    return np.array(pairs, dtype=np.int32)

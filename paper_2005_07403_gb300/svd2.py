@@ -89,6 +89,14 @@ def _declare(L):
         f = getattr(L, name)
         f.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_uint32, P]
         f.restype = ctypes.c_int
+    L.svd2_kog_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int64]
+    L.svd2_kog_workspace_bytes.restype = ctypes.c_size_t
+    for name in ("svd2_kog_step_d", "svd2_kog_step_z", "svd2_kog_step_s", "svd2_kog_step_c"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_size_t, P]
+        f.restype = ctypes.c_int
+    L.svd2_kog_skipped.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    L.svd2_kog_skipped.restype = ctypes.c_int
     for name in ("svd2_batch_s_rerun", "svd2_batch_c_rerun"):
         f = getattr(L, name)
         f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int, ctypes.c_uint32, P,
@@ -269,6 +277,47 @@ def svd2_interleaved(A: torch.Tensor, *, values_only: bool = False, backscale: b
         out.s.data_ptr(), BACKSCALE if backscale else 0, h)
     check(rc, "svd2_batch_interleaved_" + kind)
     return out
+
+
+def kog_workspace(G: torch.Tensor) -> torch.Tensor:
+    """Workspace of svd2_kog_step_* for the m x m matrix G (a uint8 device tensor)."""
+    kind = _INTERLEAVED_KIND[G.dtype]
+    nbytes = lib().svd2_kog_workspace_bytes(OPS[kind], G.shape[0])
+    return torch.empty(nbytes + 256, dtype=torch.uint8, device=G.device)
+
+
+def _aligned256(ws: torch.Tensor) -> int:
+    return (ws.data_ptr() + 255) // 256 * 256
+
+
+def kog_step(G: torch.Tensor, pairs: torch.Tensor, *, workspace: torch.Tensor | None = None,
+             stream: int | None = None) -> torch.Tensor:
+    """One parallel Kogbetliantz step (svd2_kog_step_*) in place on the square
+    CUDA tensor ``G`` (float64, float32, complex128 or complex64; row-major or
+    column-major, i.e. G or G.T contiguous up to the leading dimension) with the
+    pivot pairs ``pairs`` (int32 CUDA tensor of m entries p_0, q_0, p_1, ...).
+    Returns G."""
+    if G.dim() != 2 or G.shape[0] != G.shape[1] or not G.is_cuda:
+        raise ValueError("G must be a square CUDA matrix")
+    kind = _INTERLEAVED_KIND.get(G.dtype)
+    if kind is None:
+        raise TypeError(f"unsupported dtype {G.dtype}")
+    if pairs.dtype != torch.int32 or not pairs.is_cuda or pairs.numel() != G.shape[0]:
+        raise ValueError("pairs must be an int32 CUDA tensor with one entry per row of G")
+    rs, cs = G.stride()
+    ws = kog_workspace(G) if workspace is None else workspace
+    h = current_stream_handle(G.device) if stream is None else stream
+    rc = getattr(lib(), "svd2_kog_step_" + kind)(
+        G.shape[0], G.data_ptr(), rs, cs, pairs.contiguous().data_ptr(), _aligned256(ws),
+        ws.numel() - 256, h)
+    check(rc, "svd2_kog_step_" + kind)
+    return G
+
+
+def kog_skipped(workspace: torch.Tensor) -> int:
+    c = ctypes.c_int64()
+    check(lib().svd2_kog_skipped(_aligned256(workspace), ctypes.byref(c)), "svd2_kog_skipped")
+    return c.value
 
 
 def _host_rows(t: torch.Tensor, what: str):
