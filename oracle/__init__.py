@@ -104,6 +104,8 @@ def _declare(lib):
     lib.svd2o_bwd_d.argtypes = [_I64, pp, pp, _P, _P, pp, pp, _P, _P, pp, ctypes.c_double]
     lib.svd2o_bwd_d.restype = None
     lib.svd2o_bwd_s.argtypes = [_I64, pp, pp, _P, _P, pp, pp, _P, _P, pp, ctypes.c_float]
+    lib.svd2o_bwd_z.argtypes = [_I64, pp, pp, _P, _P, pp, pp, _P, _P, pp, ctypes.c_double]
+    lib.svd2o_bwd_c.argtypes = [_I64, pp, pp, _P, _P, pp, pp, _P, _P, pp, ctypes.c_float]
     lib.svd2o_bwd_s.restype = None
     lib.svd2o_refgrad_d.argtypes = [_I64, pp, pp, pp, _P, _P, pp, pp, ctypes.c_double]
     lib.svd2o_refgrad_d.restype = None
@@ -240,14 +242,23 @@ class Oracle:
 
 
     def bwd(self, U, V, s1, s2, gU, gV, g1, g2, rel_delta):
-        """Adjoint of the real 2x2 SVD (float64 or float32, by U's dtype).  s1, s2 are
-        back-scaled singular values.  Returns gA of shape (4, n)."""
+        """Adjoint of the 2x2 SVD (float64 or float32, by U's dtype; real with 4
+        rows, complex with 8 rows of the split layout).  s1, s2 are back-scaled
+        singular values.  Returns gA of U's shape."""
         U = np.asarray(U)
         dt = np.float64 if U.dtype == np.float64 else np.float32
-        U = _as(U, dt, 4)
-        V = _as(V, dt, 4)
-        gU = _as(gU, dt, 4)
-        gV = _as(gV, dt, 4)
+        rows = U.shape[0]
+        U = _as(U, dt, rows)
+        V = _as(V, dt, rows)
+        gU = _as(gU, dt, rows)
+        gV = _as(gV, dt, rows)
+        if rows == 8:
+            s1, s2, g1, g2 = (np.ascontiguousarray(x, dt) for x in (s1, s2, g1, g2))
+            gA = np.empty_like(U)
+            f = self.lib.svd2o_bwd_z if dt == np.float64 else self.lib.svd2o_bwd_c
+            f(U.shape[1], _ptrs(U), _ptrs(V), _p(s1), _p(s2), _ptrs(gU), _ptrs(gV),
+              _p(g1), _p(g2), _ptrs(gA), float(rel_delta))
+            return gA
         s1, s2, g1, g2 = (np.ascontiguousarray(x, dt) for x in (s1, s2, g1, g2))
         gA = np.empty_like(U)
         lib = self.lib

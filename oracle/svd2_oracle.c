@@ -613,6 +613,35 @@ void svd2o_bwd_s(int64_t n, const float *const U[4], const float *const V[4],
     }
 }
 
+/* Complex adjoint over a split-layout batch (8 rows: Re, Im of x11, x21, x12, x22). */
+#define SVD2O_BWD_CPLX(SUF, TT)                                                          \
+void svd2o_bwd_##SUF(int64_t n, const TT *const U[8], const TT *const V[8],              \
+                     const TT *s1, const TT *s2, const TT *const gU[8],                  \
+                     const TT *const gV[8], const TT *g1, const TT *g2,                  \
+                     TT *const gA[8], TT rel_delta)                                      \
+{                                                                                        \
+    _Pragma("omp parallel for schedule(static)")                                         \
+    for (int64_t k = 0; k < n; ++k) {                                                    \
+        TT ur[4], ui[4], vr[4], vi[4], gur[4], gui[4], gvr[4], gvi[4], gar[4], gai[4];   \
+        for (int e = 0; e < 4; ++e) {                                                    \
+            ur[e] = U[2 * e][k]; ui[e] = U[2 * e + 1][k];                                \
+            vr[e] = V[2 * e][k]; vi[e] = V[2 * e + 1][k];                                \
+            gur[e] = gU[2 * e][k]; gui[e] = gU[2 * e + 1][k];                            \
+            gvr[e] = gV[2 * e][k]; gvi[e] = gV[2 * e + 1][k];                            \
+        }                                                                                \
+        adjoint_cplx_##SUF##_body(ur, ui, vr, vi, s1[k], s2[k], gur, gui, gvr, gvi,      \
+                                  g1[k], g2[k], rel_delta, gar, gai);                    \
+        for (int e = 0; e < 4; ++e) {                                                    \
+            gA[2 * e][k] = gar[e];                                                       \
+            gA[2 * e + 1][k] = gai[e];                                                   \
+        }                                                                                \
+    }                                                                                    \
+}
+#define adjoint_cplx_z_body adjoint_cplx_d
+#define adjoint_cplx_c_body adjoint_cplx_s
+SVD2O_BWD_CPLX(z, double)
+SVD2O_BWD_CPLX(c, float)
+
 /*
  * Reference gradient in binary128: the paper's method run in binary128 on the
  * exactly widened double input gives U, Sigma, V to ~1e-33; the adjoint is

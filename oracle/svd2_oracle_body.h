@@ -394,3 +394,72 @@ static inline void SFX(adjoint)(const T u[4], const T v[4], T s1, T s2, const T 
     ga[2] = w11 * v21 + w12 * v22;   /* gA_12 */
     ga[3] = w21 * v21 + w22 * v22;   /* gA_22 */
 }
+
+/*
+ * Reverse-mode derivative of the complex A = U diag(s1, s2) V^* (s1 >= s2 >= 0,
+ * U and V unitary).  Elements in the record order x11, x21, x12, x22 (element
+ * (r, c) at r + 2c) with separate real and imaginary parts; every gradient g is
+ * dL/dRe + i dL/dIm (the convention under which dL = Re sum conj(g) dx).  The
+ * paper has no backward; derived from the mathematics (see the design notes):
+ * with dP = U^* dA V = Omega_U Sigma + dSigma - Sigma Omega_V (Omega_U = U^* dU,
+ * Omega_V = V^* dV skew-Hermitian), J = U^* gU, K = V^* gV,
+ *   a = J12 - conj(J21), b = K12 - conj(K21),
+ *   p = (a - b) / (2 (s1 + s2)), q = (a + b) / (2 (s1 - s2)),
+ *   M = [[g1 + i t1, p - q], [-conj(p) - conj(q), g2 + i t2]],
+ *   t_i = (Im J_ii - Im K_ii) / (2 s_i)   (0 when s_i = 0),
+ *   gA = U M V^*.
+ * The diagonal terms t_i carry the phase gauge (U, V -> U D, V D for a unitary
+ * diagonal D): for a loss that is invariant under it Im J_ii + Im K_ii = 0 and
+ * t_i = Im J_ii / s_i.  1/(s1 - s2) is safeguarded as in the real adjoint, and
+ * for real data the result is the real adjoint's.
+ */
+static inline void SFX(adjoint_cplx)(const T ur[4], const T ui[4], const T vr[4], const T vi[4],
+                              T s1, T s2, const T gur[4], const T gui[4], const T gvr[4],
+                              const T gvi[4], T g1, T g2, T dl, T gar[4], T gai[4])
+{
+    /* J_xy = sum_a conj(u_ax) gu_ay, element (a, x) at a + 2x */
+    const T Jr12 = (ur[0] * gur[2] + ui[0] * gui[2]) + (ur[1] * gur[3] + ui[1] * gui[3]);
+    const T Ji12 = (ur[0] * gui[2] - ui[0] * gur[2]) + (ur[1] * gui[3] - ui[1] * gur[3]);
+    const T Jr21 = (ur[2] * gur[0] + ui[2] * gui[0]) + (ur[3] * gur[1] + ui[3] * gui[1]);
+    const T Ji21 = (ur[2] * gui[0] - ui[2] * gur[0]) + (ur[3] * gui[1] - ui[3] * gur[1]);
+    const T Ji11 = (ur[0] * gui[0] - ui[0] * gur[0]) + (ur[1] * gui[1] - ui[1] * gur[1]);
+    const T Ji22 = (ur[2] * gui[2] - ui[2] * gur[2]) + (ur[3] * gui[3] - ui[3] * gur[3]);
+    const T Kr12 = (vr[0] * gvr[2] + vi[0] * gvi[2]) + (vr[1] * gvr[3] + vi[1] * gvi[3]);
+    const T Ki12 = (vr[0] * gvi[2] - vi[0] * gvr[2]) + (vr[1] * gvi[3] - vi[1] * gvr[3]);
+    const T Kr21 = (vr[2] * gvr[0] + vi[2] * gvi[0]) + (vr[3] * gvr[1] + vi[3] * gvi[1]);
+    const T Ki21 = (vr[2] * gvi[0] - vi[2] * gvr[0]) + (vr[3] * gvi[1] - vi[3] * gvr[1]);
+    const T Ki11 = (vr[0] * gvi[0] - vi[0] * gvr[0]) + (vr[1] * gvi[1] - vi[1] * gvr[1]);
+    const T Ki22 = (vr[2] * gvi[2] - vi[2] * gvr[2]) + (vr[3] * gvi[3] - vi[3] * gvr[3]);
+    /* a = J12 - conj(J21), b = K12 - conj(K21) */
+    const T ar = Jr12 - Jr21, ai = Ji12 + Ji21;
+    const T br = Kr12 - Kr21, bi = Ki12 + Ki21;
+    const T sum = s1 + s2;
+    const T inv_sum = sum > (T)0 ? (T)1 / sum : (T)0;
+    T inv_gap = (T)0;
+    if (s1 > (T)0) {
+        const T g = (s1 - s2) / s1;
+        inv_gap = g / (s1 * (g * g + dl * dl));
+    }
+    const T pr = (T)0.5 * (ar - br) * inv_sum, pi = (T)0.5 * (ai - bi) * inv_sum;
+    const T qr = (T)0.5 * (ar + br) * inv_gap, qi = (T)0.5 * (ai + bi) * inv_gap;
+    const T t1 = s1 > (T)0 ? (T)0.5 * (Ji11 - Ki11) / s1 : (T)0;
+    const T t2 = s2 > (T)0 ? (T)0.5 * (Ji22 - Ki22) / s2 : (T)0;
+    /* M in the record order m11, m21, m12, m22 */
+    const T mr[4] = { g1, -pr - qr, pr - qr, g2 };
+    const T mi[4] = { t1, pi + qi, pi - qi, t2 };
+    /* W = U M: w_xy = u_x1 m_1y + u_x2 m_2y */
+    T wr[4], wi[4];
+    for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 2; ++y) {
+            const int o = x + 2 * y, u1 = x, u2 = x + 2, m1 = 2 * y, m2 = 2 * y + 1;
+            wr[o] = (ur[u1] * mr[m1] - ui[u1] * mi[m1]) + (ur[u2] * mr[m2] - ui[u2] * mi[m2]);
+            wi[o] = (ur[u1] * mi[m1] + ui[u1] * mr[m1]) + (ur[u2] * mi[m2] + ui[u2] * mr[m2]);
+        }
+    /* gA = W V^*: ga_xy = w_x1 conj(v_y1) + w_x2 conj(v_y2) */
+    for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 2; ++y) {
+            const int o = x + 2 * y, w1 = x, w2 = x + 2, v1 = y, v2 = y + 2;
+            gar[o] = (wr[w1] * vr[v1] + wi[w1] * vi[v1]) + (wr[w2] * vr[v2] + wi[w2] * vi[v2]);
+            gai[o] = (wi[w1] * vr[v1] - wr[w1] * vi[v1]) + (wi[w2] * vr[v2] - wr[w2] * vi[v2]);
+        }
+}
