@@ -382,6 +382,24 @@ def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
         out[name] = {"fwd_bwd_matrices_per_s": n / (ms / 1e3), "fwd_bwd_ms": ms,
                      "bwd_ms": ms - msf}
         del A, gU, gV, gS, r, gA
+    # complex: N(0,1) parts and upstream gradients drawn on the device
+    for name, dt in (("complex128", torch.float64), ("complex64", torch.float32)):
+        A = inputs.normal_batch_device(n, 8, 151, "cuda", dt)
+        gU = inputs.normal_batch_device(n, 8, 152, "cuda", dt)
+        gV = inputs.normal_batch_device(n, 8, 153, "cuda", dt)
+        gS = inputs.normal_batch_device(n, 2, 154, "cuda", dt)
+        r = S.empty_result(8, n, dt, A.device)
+        gA = torch.empty_like(A)
+
+        def step():
+            S.svd2(A, backscale=True, out=r)
+            S.svd2_bwd(r.U, r.V, r.smax, r.smin, gU, gV, gS[0], gS[1], out=gA)
+
+        ms = time_steps(torch, step, steps, warmup, stream)
+        msf = time_steps(torch, lambda: S.svd2(A, backscale=True, out=r), steps, warmup, stream)
+        out[name] = {"fwd_bwd_matrices_per_s": n / (ms / 1e3), "fwd_bwd_ms": ms,
+                     "bwd_ms": ms - msf}
+        del A, gU, gV, gS, r, gA
     torch.cuda.empty_cache()
     return out
 

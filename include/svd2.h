@@ -249,6 +249,31 @@ int svd2_bwd_s(int64_t n, const float *const U[4], const float *const V[4],
                float *const gA[4], float rel_delta, svd2_stream_t stream);
 
 /*
+ * Backward of the complex 2x2 SVD, FP64 and FP32 (split layout, 8 arrays each
+ * for U, V, gU, gV, gA: real and imaginary parts of u11, u21, u12, u22).
+ * Gradients are dL/dRe + i dL/dIm (so the real and imaginary rows of gA are
+ * the derivatives with respect to the real and imaginary rows of A).  For
+ * A = U diag(s1, s2) V^*, J = U^* gU, K = V^* gV, a = J12 - conj(J21),
+ * b = K12 - conj(K21), p, q as in svd2_bwd_d (complex now, same safeguard):
+ *   gA = U M V^*,  M = [[g1 + i t1, p - q], [-conj(p) - conj(q), g2 + i t2]],
+ *   t_i = (Im J_ii - Im K_ii) / (2 s_i)   (0 when s_i = 0).
+ * The singular vectors are determined only up to the phase gauge
+ * U, V -> U D, V D (D unitary diagonal); the t_i terms are exact for losses
+ * invariant under it (then Im J_ii + Im K_ii = 0), the losses whose
+ * derivative is defined.  For real data the result is svd2_bwd_d's.  The
+ * paper defines no backward.  Arguments, NULL gradients and errors as
+ * svd2_bwd_d.
+ */
+int svd2_bwd_z(int64_t n, const double *const U[8], const double *const V[8],
+               const double *s1, const double *s2, const double *const gU[8],
+               const double *const gV[8], const double *g1, const double *g2,
+               double *const gA[8], double rel_delta, svd2_stream_t stream);
+int svd2_bwd_c(int64_t n, const float *const U[8], const float *const V[8],
+               const float *s1, const float *s2, const float *const gU[8],
+               const float *const gV[8], const float *g1, const float *g2,
+               float *const gA[8], float rel_delta, svd2_stream_t stream);
+
+/*
  * Many batches in one persistent launch (the batches of one or more parallel
  * Kogbetliantz steps, Sec. 1), real FP64 and complex FP64 mixed.  Each batch is
  * described as for svd2_batch_d / svd2_batch_z; the batches are cut into tiles

@@ -1,8 +1,9 @@
-"""torch.autograd.Function around the batched real 2x2 SVD.
+"""torch.autograd.Function around the batched 2x2 SVD (real and complex).
 
 Forward: the CUDA forward kernel with back-scaling (Fig. 1), so the singular
-values are those of A itself.  Backward: the hand-written adjoint kernel
-(svd2_bwd_d / svd2_bwd_s) with the near-equal singular value safeguard.
+values are those of A itself.  Backward: the hand-written adjoint kernels
+(svd2_bwd_{d,s,z,c}) with the near-equal singular value safeguard; for
+complex data, with the phase-gauge terms (exact for gauge-invariant losses).
 The singular vectors of the method are fixed by its pivoting and sign choices
 (Eq. 29), which are locally constant, so the map A -> (U, S, V) is smooth
 wherever those choices and s1 != s2 hold, and the adjoint is its derivative.
@@ -34,9 +35,12 @@ class Svd2Fn(torch.autograd.Function):
 
 
 def svd2(A: torch.Tensor, rel_delta: float | None = None):
-    """Differentiable batched SVD of real 2x2 matrices in the split layout:
-    A (4, n) float64/float32 on a CUDA device -> (U (4, n), S (2, n), V (4, n))
-    with A = U diag(S) V^T per matrix."""
-    if A.dim() != 2 or A.shape[0] != 4:
-        raise ValueError("A must have shape (4, n) (real matrices)")
+    """Differentiable batched SVD of 2x2 matrices in the split layout: A (4, n)
+    real or (8, n) complex (real and imaginary rows), float64/float32 on a CUDA
+    device -> (U, S (2, n), V) with A = U diag(S) V^* per matrix.  For complex
+    data the gradient rows are dL/dRe and dL/dIm; a loss of U and V should be
+    invariant under the phase gauge U, V -> U D, V D for its gradient to be
+    defined."""
+    if A.dim() != 2 or A.shape[0] not in (4, 8):
+        raise ValueError("A must have shape (4, n) or (8, n)")
     return Svd2Fn.apply(A, rel_delta)

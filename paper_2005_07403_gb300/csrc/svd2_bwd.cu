@@ -86,6 +86,147 @@ __global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs<T> p) {
   }
 }
 
+// Complex adjoint (svd2_bwd_z / svd2_bwd_c): with J = U^* gU, K = V^* gV,
+// a = J12 - conj(J21), b = K12 - conj(K21), p and q as in the real case,
+//   gA = U M V^*,  M = [[g1 + i t1, p - q], [-conj(p) - conj(q), g2 + i t2]],
+//   t_i = (Im J_ii - Im K_ii) / (2 s_i) (0 for s_i = 0),
+// gradients as dL/dRe + i dL/dIm.  The t_i carry the phase gauge
+// U, V -> U D, V D: for a loss invariant under it, Im J_ii + Im K_ii = 0.
+// Same order of correctly rounded operations as the oracle's complex adjoint.
+template <typename T>
+struct BwdArgsC {
+  const T *u[8];
+  const T *v[8];
+  const T *s1;
+  const T *s2;
+  const T *gu[8];
+  const T *gv[8];
+  const T *g1;
+  const T *g2;
+  T *ga[8];
+  T dl;
+  int64_t n;
+};
+
+// sum_a conj(x_a) y_a over the two elements (a0, a1) of x and (b0, b1) of y:
+// real part (xr yr + xi yi) + (..), imaginary part (xr yi - xi yr) + (..).
+template <typename T>
+__device__ __forceinline__ T cdot_re(T xr0, T xi0, T yr0, T yi0, T xr1, T xi1, T yr1, T yi1) {
+  using F = fp<T>;
+  return F::add(F::add(F::mul(xr0, yr0), F::mul(xi0, yi0)), F::add(F::mul(xr1, yr1), F::mul(xi1, yi1)));
+}
+template <typename T>
+__device__ __forceinline__ T cdot_im(T xr0, T xi0, T yr0, T yi0, T xr1, T xi1, T yr1, T yi1) {
+  using F = fp<T>;
+  return F::add(F::sub(F::mul(xr0, yi0), F::mul(xi0, yr0)), F::sub(F::mul(xr1, yi1), F::mul(xi1, yr1)));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) bwd_cplx_kernel(const BwdArgsC<T> p) {
+  using F = fp<T>;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride) {
+    T ur[4], ui[4], vr[4], vi[4], gur[4], gui[4], gvr[4], gvi[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ur[e] = __ldcs(p.u[2 * e] + k);
+      ui[e] = __ldcs(p.u[2 * e + 1] + k);
+      vr[e] = __ldcs(p.v[2 * e] + k);
+      vi[e] = __ldcs(p.v[2 * e + 1] + k);
+      gur[e] = ld0(p.gu[2 * e], k);
+      gui[e] = ld0(p.gu[2 * e + 1], k);
+      gvr[e] = ld0(p.gv[2 * e], k);
+      gvi[e] = ld0(p.gv[2 * e + 1], k);
+    }
+    const T s1 = __ldcs(p.s1 + k), s2 = __ldcs(p.s2 + k);
+    // J_xy = sum_a conj(u_ax) gu_ay, element (a, x) at a + 2x
+    const T Jr12 = cdot_re(ur[0], ui[0], gur[2], gui[2], ur[1], ui[1], gur[3], gui[3]);
+    const T Ji12 = cdot_im(ur[0], ui[0], gur[2], gui[2], ur[1], ui[1], gur[3], gui[3]);
+    const T Jr21 = cdot_re(ur[2], ui[2], gur[0], gui[0], ur[3], ui[3], gur[1], gui[1]);
+    const T Ji21 = cdot_im(ur[2], ui[2], gur[0], gui[0], ur[3], ui[3], gur[1], gui[1]);
+    const T Ji11 = cdot_im(ur[0], ui[0], gur[0], gui[0], ur[1], ui[1], gur[1], gui[1]);
+    const T Ji22 = cdot_im(ur[2], ui[2], gur[2], gui[2], ur[3], ui[3], gur[3], gui[3]);
+    const T Kr12 = cdot_re(vr[0], vi[0], gvr[2], gvi[2], vr[1], vi[1], gvr[3], gvi[3]);
+    const T Ki12 = cdot_im(vr[0], vi[0], gvr[2], gvi[2], vr[1], vi[1], gvr[3], gvi[3]);
+    const T Kr21 = cdot_re(vr[2], vi[2], gvr[0], gvi[0], vr[3], vi[3], gvr[1], gvi[1]);
+    const T Ki21 = cdot_im(vr[2], vi[2], gvr[0], gvi[0], vr[3], vi[3], gvr[1], gvi[1]);
+    const T Ki11 = cdot_im(vr[0], vi[0], gvr[0], gvi[0], vr[1], vi[1], gvr[1], gvi[1]);
+    const T Ki22 = cdot_im(vr[2], vi[2], gvr[2], gvi[2], vr[3], vi[3], gvr[3], gvi[3]);
+    const T ar = F::sub(Jr12, Jr21), ai = F::add(Ji12, Ji21);
+    const T br = F::sub(Kr12, Kr21), bi = F::add(Ki12, Ki21);
+    const T sum = F::add(s1, s2);
+    const T inv_sum = sum > T(0) ? F::div(T(1), sum) : T(0);
+    T inv_gap = T(0);
+    if (s1 > T(0)) {
+      const T g = F::div(F::sub(s1, s2), s1);
+      inv_gap = F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
+    }
+    const T pr = F::mul(F::mul(T(0.5), F::sub(ar, br)), inv_sum);
+    const T pi = F::mul(F::mul(T(0.5), F::sub(ai, bi)), inv_sum);
+    const T qr = F::mul(F::mul(T(0.5), F::add(ar, br)), inv_gap);
+    const T qi = F::mul(F::mul(T(0.5), F::add(ai, bi)), inv_gap);
+    const T t1 = s1 > T(0) ? F::div(F::mul(T(0.5), F::sub(Ji11, Ki11)), s1) : T(0);
+    const T t2 = s2 > T(0) ? F::div(F::mul(T(0.5), F::sub(Ji22, Ki22)), s2) : T(0);
+    // M in the record order m11, m21, m12, m22
+    const T mr[4] = {ld0(p.g1, k), F::sub(b_neg(pr), qr), F::sub(pr, qr), ld0(p.g2, k)};
+    const T mi[4] = {t1, F::add(pi, qi), F::sub(pi, qi), t2};
+    // W = U M
+    T wr[4], wi[4];
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+#pragma unroll
+      for (int y = 0; y < 2; ++y) {
+        const int o = x + 2 * y, u1 = x, u2 = x + 2, m1 = 2 * y, m2 = 2 * y + 1;
+        wr[o] = F::add(F::sub(F::mul(ur[u1], mr[m1]), F::mul(ui[u1], mi[m1])),
+                       F::sub(F::mul(ur[u2], mr[m2]), F::mul(ui[u2], mi[m2])));
+        wi[o] = F::add(F::add(F::mul(ur[u1], mi[m1]), F::mul(ui[u1], mr[m1])),
+                       F::add(F::mul(ur[u2], mi[m2]), F::mul(ui[u2], mr[m2])));
+      }
+    }
+    // gA = W V^*
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+#pragma unroll
+      for (int y = 0; y < 2; ++y) {
+        const int o = x + 2 * y, w1 = x, w2 = x + 2, v1 = y, v2 = y + 2;
+        __stcs(p.ga[2 * o] + k, F::add(F::add(F::mul(wr[w1], vr[v1]), F::mul(wi[w1], vi[v1])),
+                                       F::add(F::mul(wr[w2], vr[v2]), F::mul(wi[w2], vi[v2]))));
+        __stcs(p.ga[2 * o + 1] + k, F::add(F::sub(F::mul(wi[w1], vr[v1]), F::mul(wr[w1], vi[v1])),
+                                           F::sub(F::mul(wi[w2], vr[v2]), F::mul(wr[w2], vi[v2]))));
+      }
+    }
+  }
+}
+
+template <typename T>
+static int launch_bwd_cplx(int64_t n, const T *const *U, const T *const *V, const T *s1,
+                           const T *s2, const T *const *gU, const T *const *gV, const T *g1,
+                           const T *g2, T *const *gA, T rel_delta, cudaStream_t stream) {
+  if (n < 0 || !(rel_delta >= T(0))) return SVD2_EINVAL;
+  if (n == 0) return SVD2_OK;
+  if (!U || !V || !gA || !s1 || !s2) return SVD2_EINVAL;
+  BwdArgsC<T> p{};
+  for (int e = 0; e < 8; ++e) {
+    if (!U[e] || !V[e] || !gA[e]) return SVD2_EINVAL;
+    p.u[e] = U[e];
+    p.v[e] = V[e];
+    p.gu[e] = gU ? gU[e] : nullptr;
+    p.gv[e] = gV ? gV[e] : nullptr;
+    p.ga[e] = gA[e];
+  }
+  p.s1 = s1;
+  p.s2 = s2;
+  p.g1 = g1;
+  p.g2 = g2;
+  p.dl = rel_delta;
+  p.n = n;
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  bwd_cplx_kernel<T><<<(unsigned)(want < cap ? want : cap), 256, 0, stream>>>(p);
+  SVD2_CUDA_TRY(cudaGetLastError());
+  return SVD2_OK;
+}
+
 template <typename T>
 static int launch_bwd(int64_t n, const T *const *U, const T *const *V, const T *s1, const T *s2,
                       const T *const *gU, const T *const *gV, const T *g1, const T *g2,
@@ -132,4 +273,20 @@ extern "C" int svd2_bwd_s(int64_t n, const float *const U[4], const float *const
                           const float *const gV[4], const float *g1, const float *g2,
                           float *const gA[4], float rel_delta, svd2_stream_t stream) {
   return launch_bwd<float>(n, U, V, s1, s2, gU, gV, g1, g2, gA, rel_delta, (cudaStream_t)stream);
+}
+
+extern "C" int svd2_bwd_z(int64_t n, const double *const U[8], const double *const V[8],
+                          const double *s1, const double *s2, const double *const gU[8],
+                          const double *const gV[8], const double *g1, const double *g2,
+                          double *const gA[8], double rel_delta, svd2_stream_t stream) {
+  return launch_bwd_cplx<double>(n, U, V, s1, s2, gU, gV, g1, g2, gA, rel_delta,
+                                 (cudaStream_t)stream);
+}
+
+extern "C" int svd2_bwd_c(int64_t n, const float *const U[8], const float *const V[8],
+                          const float *s1, const float *s2, const float *const gU[8],
+                          const float *const gV[8], const float *g1, const float *g2,
+                          float *const gA[8], float rel_delta, svd2_stream_t stream) {
+  return launch_bwd_cplx<float>(n, U, V, s1, s2, gU, gV, g1, g2, gA, rel_delta,
+                                (cudaStream_t)stream);
 }

@@ -134,6 +134,10 @@ def _declare(L):
     L.svd2_bwd_d.restype = ctypes.c_int
     L.svd2_bwd_s.argtypes = [ctypes.c_int64, PP, PP, P, P, PP, PP, P, P, PP, ctypes.c_float, P]
     L.svd2_bwd_s.restype = ctypes.c_int
+    L.svd2_bwd_z.argtypes = [ctypes.c_int64, PP, PP, P, P, PP, PP, P, P, PP, ctypes.c_double, P]
+    L.svd2_bwd_z.restype = ctypes.c_int
+    L.svd2_bwd_c.argtypes = [ctypes.c_int64, PP, PP, P, P, PP, PP, P, P, PP, ctypes.c_float, P]
+    L.svd2_bwd_c.restype = ctypes.c_int
     L.svd2_batch_host.argtypes = [ctypes.c_int, ctypes.c_int64, PP, PP, PP, P, P, P,
                                   ctypes.c_uint32, ctypes.c_int64, P]
     L.svd2_batch_host.restype = ctypes.c_int
@@ -420,17 +424,18 @@ def _opt_rows(t, n, what):
 
 def svd2_bwd(U, V, s1, s2, gU=None, gV=None, g1=None, g2=None, rel_delta=None,
              out: torch.Tensor | None = None, stream: int | None = None) -> torch.Tensor:
-    """Adjoint of the real 2x2 SVD (svd2_bwd_d / svd2_bwd_s): gA (4, n) from U, V
-    (4, n), the singular values s1, s2 (n,) and the upstream gradients (None =
-    zero)."""
+    """Adjoint of the 2x2 SVD (svd2_bwd_{d,s,z,c}): gA of U's shape from U, V
+    ((4, n) real or (8, n) complex split layout), the singular values s1, s2
+    (n,) and the upstream gradients (None = zero); for complex data the rows
+    of a gradient are dL/dRe and dL/dIm of the corresponding rows."""
     rows, n = U.shape
-    if rows != 4 or U.dtype not in (torch.float64, torch.float32):
-        raise ValueError("svd2_bwd takes real (4, n) float64/float32 factors")
+    if rows not in (4, 8) or U.dtype not in (torch.float64, torch.float32):
+        raise ValueError("svd2_bwd takes (4, n) or (8, n) float64/float32 factors")
     if rel_delta is None:
         rel_delta = default_rel_delta(U.dtype)
     if out is None:
         out = torch.empty_like(U)
-    f = lib().svd2_bwd_d if U.dtype == torch.float64 else lib().svd2_bwd_s
+    f = getattr(lib(), "svd2_bwd_" + _kind(rows, U.dtype))
     h = current_stream_handle(U.device) if stream is None else stream
     p = lambda t: None if t is None else t.data_ptr()  # noqa: E731
     rc = f(n, ptr_array(_rows(U, "U")), ptr_array(_rows(V, "V")), s1.data_ptr(), s2.data_ptr(),
