@@ -342,7 +342,10 @@ int svd2_multi_autotune(const svd2_batch_desc *descs, int32_t nbatch, void *plan
 /*
  * The forward forms (op 0 = d, 1 = z, 2 = s, 3 = c) on a batch held in HOST
  * memory: A, U, V are host arrays of host element pointers, smax, smin, s host
- * arrays, in the layout above.  The batch is cut into chunks of `chunk`
+ * arrays, in the layout above.  When every array is page-locked host memory
+ * (cudaHostAlloc, cudaMallocHost, cudaHostRegister; checked with
+ * cudaPointerGetAttributes), the kernel reads and writes the arrays directly
+ * across the host link and `chunk` is unused.  Otherwise the batch is cut into chunks of `chunk`
  * matrices (0 = 2^21; rounded up to a multiple of 64) that are copied to the
  * device, decomposed and copied back through a double-buffered three-stream
  * pipeline, so the copies in both directions overlap the kernels.  The call is
