@@ -116,15 +116,22 @@ GB300_SM_MAX_MHZ = 2070.0
 FP64_OPS_PER_MATRIX = {"z": 91, "d": 34}
 
 
-def sources_digest():
-    """SHA-256 over the CUDA sources, the C header and the build script: the
-    DRAM traffic recorded under profiles/ holds only for this exact digest."""
+# The translation unit each workload's kernels are built from; every digest
+# also covers the shared headers, the C header and the build script.
+KERNEL_SOURCES = {"complex128": "svd2_fwd_z.cu", "real-fp64": "svd2_fwd_d.cu",
+                  "real-fp32": "svd2_fwd_s.cu", "real-fp32-rerun": "svd2_rerun.cu"}
+
+
+def sources_digest(workload):
+    """SHA-256 over the sources of the workload's kernels: the DRAM traffic
+    recorded under profiles/ holds only for this exact digest."""
     import hashlib
     h = hashlib.sha256()
-    files = [os.path.join("include", "svd2.h"), os.path.join("paper_2005_07403_gb300", "build.py")]
     csrc = os.path.join("paper_2005_07403_gb300", "csrc")
+    files = [os.path.join("include", "svd2.h"), os.path.join("paper_2005_07403_gb300", "build.py"),
+             os.path.join(csrc, KERNEL_SOURCES[workload])]
     files += sorted(os.path.join(csrc, f) for f in os.listdir(os.path.join(ROOT, csrc))
-                    if f.endswith((".cu", ".cuh")))
+                    if f.endswith(".cuh"))
     for rel in files:
         h.update(rel.encode())
         with open(os.path.join(ROOT, rel), "rb") as f:
@@ -141,7 +148,7 @@ def recorded_traffic(workload, n):
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    digest = sources_digest()
+    digest = sources_digest(workload)
     for ln in lines:
         f = ln.split()
         if len(f) >= 6 and not ln.startswith("#") and f[0] == workload and f[1] == digest:
@@ -617,7 +624,8 @@ def run_ours(args):
 
 def main():
     if "--sources-digest" in sys.argv:
-        print(sources_digest())
+        for w in KERNEL_SOURCES:
+            print(w, sources_digest(w))
         return
     args = parse()
     if args.impl == "reference":
