@@ -209,7 +209,8 @@ int svd2_rerun_count(const void *workspace, int64_t *count);
  * cudaMalloc once running (cudaMalloc may synchronise the device, which a
  * latency-bound loop or a fixed start-up memory budget cannot accept).  The
  * paper has no counterpart; it is a deployment variant of the re-run form.
- * The scratch (counters and index list) is a fixed array of about 4 MiB in
+ * The scratch (sized by the workspace formula of svd2_batch_s_rerun for
+ * SVD2_NOALLOC_MAX_N matrices) is a fixed array of about 4 MiB in
  * device memory, reserved on every device that loads the library until the
  * process exits; n is limited to SVD2_NOALLOC_MAX_N matrices (larger n returns
  * SVD2_ETOOBIG) -- split larger batches, or use svd2_batch_s_rerun.  The first

@@ -1,17 +1,20 @@
 // FP32 form with FP64 re-run: svd2_batch_s_rerun / svd2_batch_c_rerun.
 //
-// One kernel.  Each block takes tiles of consecutive matrices; for a tile it
-// first runs the single-precision method (Sec. 1, Sec. 7) on every matrix and
-// flags each matrix whose scaled singular values satisfy
-// sigma'_min < 2^tau sigma'_max (compared in float; the product by the power of
-// two is exact), queueing its index and input elements in shared memory.
-// After a barrier the whole block re-runs the queued matrices, on full warps,
-// with the double-precision method on the exactly widened input, and
-// overwrites their outputs with the double results rounded to float, sigma'
-// brought to the float run's scale: sigma'_32 = RN32(sigma'_64 2^(s32 - s64)).
-// The re-run reads its inputs from shared memory and writes lines the block
-// has just written (still in L2), so it adds no scattered DRAM traffic.  The
-// number of re-run matrices is accumulated in the workspace.
+// Each block takes tiles of consecutive matrices; for a tile it first runs the
+// single-precision method (Sec. 1, Sec. 7) on every matrix and flags each
+// matrix whose scaled singular values satisfy sigma'_min < 2^tau sigma'_max
+// (compared in float; the product by the power of two is exact), queueing its
+// index and input elements in shared memory.  Once the queue holds a block's
+// worth (and at the end), the whole block re-runs the queued matrices, on
+// full warps, with the double-precision method on the exactly widened input,
+// and overwrites their outputs with the double results rounded to float,
+// sigma' brought to the float run's scale: sigma'_32 = RN32(sigma'_64
+// 2^(s32 - s64)).  The re-run reads its inputs from shared memory; its
+// scattered stores rewrite lines the block wrote a few tiles earlier, part of
+// which have left L2 by then (measured: +74% DRAM reads, +27% writes over
+// the algorithmic bytes).  The number of re-run matrices is accumulated in
+// the workspace.  A second kernel, the fix-up pass, finishes the matrices the
+// fast arithmetic of either precision could not (reads one word otherwise).
 #include "svd2_fwd_impl.cuh"
 
 namespace svd2 {
