@@ -123,8 +123,9 @@ KERNEL_SOURCES = {"complex128": "svd2_fwd_z.cu", "real-fp64": "svd2_fwd_d.cu",
 
 
 def sources_digest(workload):
-    """SHA-256 over the sources of the workload's kernels: the DRAM traffic
-    recorded under profiles/ holds only for this exact digest."""
+    """SHA-256 over the code (comments and blank space removed) of the
+    workload's kernel sources: the DRAM traffic recorded under profiles/ holds
+    only for this exact digest."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join("paper_2005_07403_gb300", "csrc")
@@ -132,10 +133,19 @@ def sources_digest(workload):
              os.path.join(csrc, KERNEL_SOURCES[workload])]
     files += sorted(os.path.join(csrc, f) for f in os.listdir(os.path.join(ROOT, csrc))
                     if f.endswith(".cuh"))
+    import re
     for rel in files:
         h.update(rel.encode())
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            text = f.read()
+        # the code only: comments and blank space do not change a kernel
+        if rel.endswith(".py"):
+            text = re.sub(r'(?s)""".*?"""', "", text)
+            text = re.sub(r"#[^\n]*", "", text)
+        else:
+            text = re.sub(r"(?s)/\*.*?\*/", "", text)
+            text = re.sub(r"//[^\n]*", "", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
