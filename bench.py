@@ -221,20 +221,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cores():
+    """Host cores available to this process (an inherited OMP_NUM_THREADS, which
+    torchrun sets to 1, does not limit the oracle's timing)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(A, rows, min_seconds=10.0, sample=2**21):
     """The oracle as it stands, on all host cores, over a bounded sample of the
     workload (the first `sample` matrices), repeated for at least min_seconds."""
     import oracle
+    cores = host_cores()
     S = np.ascontiguousarray(A[:, :sample])
-    oracle.svd2(S[:, :1024])          # build/load outside the timing
+    oracle.svd2(S[:, :1024], nthreads=cores)          # build/load outside the timing
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.svd2(S)
+        oracle.svd2(S, nthreads=cores)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
             break
-    return {"value": reps * S.shape[1] / el, "unit": "matrices/s", "cores": oracle.max_threads(),
+    return {"value": reps * S.shape[1] / el, "unit": "matrices/s", "cores": cores,
             "kind": "oracle",
             "sample": f"first {S.shape[1]} matrices of the workload, {reps} passes, {el:.1f} s"}
 
@@ -244,15 +254,16 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    cores = host_cores()
     W = WORKLOADS[args.workload]
     sample = 2**21
     A = make_input(args.workload, sample, 0)
     if W["form"] == "rerun":
         def run(a):
-            return oracle.svd2_rerun(a, -8)
+            return oracle.svd2_rerun(a, -8, nthreads=cores)
     else:
         def run(a):
-            return oracle.svd2(a)
+            return oracle.svd2(a, nthreads=cores)
     run(np.ascontiguousarray(A[:, :1024]))
     for _ in range(args.warmup):
         run(A)
@@ -267,7 +278,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
             "config": {"workload": W["desc"], "sample_per_step": sample},
             "cpu_baseline": {"value": value, "unit": "matrices/s", "kind": "oracle",
-                             "cores": oracle.max_threads(),
+                             "cores": cores,
                              "sample": f"{sample} matrices of the workload per step"},
             "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
