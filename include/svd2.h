@@ -275,21 +275,24 @@ int svd2_bwd_c(int64_t n, const float *const U[8], const float *const V[8],
                float *const gA[8], float rel_delta, svd2_stream_t stream);
 
 /*
- * Many batches in one persistent launch (the batches of one or more parallel
- * Kogbetliantz steps, Sec. 1), real FP64 and complex FP64 mixed.  Each batch is
- * described as for svd2_batch_d / svd2_batch_z; the batches are cut into tiles
- * of block * mpt * unroll matrices and a persistent grid walks the tiles in a
- * fixed round-robin order (no atomics, no scratch, deterministic; the results
- * equal those of one svd2_batch_d / svd2_batch_z call per batch).
+ * Many batches in one launch (the batches of one or more parallel Kogbetliantz
+ * steps, Sec. 1), real FP64 and complex FP64 mixed.  Each batch is described
+ * as for svd2_batch_d / svd2_batch_z; the batches are cut into tiles of
+ * block * mpt * unroll matrices and the grid walks the tiles in a fixed
+ * round-robin order (no atomics, no scratch, deterministic; the results equal
+ * those of one svd2_batch_d / svd2_batch_z call per batch).
  *
  * svd2_multi_plan_bytes(nbatch): device bytes of a plan for nbatch batches.
  * svd2_multi_prepare: writes the plan for this launch shape (block a multiple
  *   of 32 in 32..512, mpt in {1, 2}, unroll in {1, 2}) to the caller-owned
  *   device buffer `plan` (16-byte aligned) with a synchronous copy, and returns
  *   the tile count in *total_tiles (may be NULL).  descs is a host array.
- * svd2_multi_run: one persistent launch over the plan, asynchronous on
+ * svd2_multi_run: one launch per kind over the plan, asynchronous on
  *   `stream`; block, mpt and unroll must be those of the plan (otherwise the
- *   launch does nothing); grid 0 = SMs x resident blocks per SM.
+ *   launch does nothing).  grid 0: one block per tile for a plan prepared in
+ *   this process (the tile counts are remembered on the host; the fastest on
+ *   GB300), else SMs x resident blocks; grid > 0: that many blocks, a
+ *   persistent grid walking the tiles when it is at most the resident count.
  * svd2_multi_graph_create: the same launch captured into an executable CUDA
  *   graph (*graph_exec), replayed with svd2_graph_launch and freed with
  *   svd2_graph_destroy.  The plan and the batch arrays must stay allocated

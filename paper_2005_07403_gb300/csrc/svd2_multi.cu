@@ -7,16 +7,19 @@
 // batch costs a launch and a tail of idle SMs per batch, which dominates for
 // short batches.  Here the batches of a step are cut into tiles of
 // block * mpt * unroll consecutive matrices; tile t of the concatenated tile
-// sequence belongs to the batch whose tile prefix range holds it.  A grid of
-// (SMs x resident blocks) CTAs walks the tiles in a fixed round-robin order,
-// CTA c taking tiles c, c + grid, c + 2 grid, ...: no atomics, no scratch
-// memory, the same assignment on every launch, so the launch can be captured
-// once in a CUDA graph and replayed every step.  Real and complex batches form
+// sequence belongs to the batch whose tile prefix range holds it.  CTA c takes
+// tiles c, c + grid, c + 2 grid, ... -- by default one CTA per tile, or a
+// persistent grid of a given size: no atomics, no scratch memory, the same
+// assignment on every launch, so the launch can be captured once in a CUDA
+// graph and replayed every step.  Real and complex batches form
 // two tile sequences, each walked by its own persistent kernel (launched one
 // after the other), so each kernel carries only its own variant of the method
 // and keeps its own register budget.
 #include <cstddef>
+#include <mutex>
 #include <new>
+#include <unordered_map>
+#include <utility>
 
 #include "svd2_common.cuh"
 #include "svd2_fwd_impl.cuh"
@@ -108,7 +111,7 @@ __device__ __forceinline__ void multi_group(const MultiBatch &b, int64_t k0, int
 }
 
 template <bool CPLX, int M, int UNR>
-__global__ void __launch_bounds__(512, CPLX ? 2 : 1) multi_kernel(const unsigned char *plan) {
+__global__ void __launch_bounds__(512, 2) multi_kernel(const unsigned char *plan) {
   const MultiPlanHeader &h = *reinterpret_cast<const MultiPlanHeader *>(plan);
   const MultiBatch *batches = reinterpret_cast<const MultiBatch *>(plan + kPlanHeader);
   const int b_end = CPLX ? h.nbatch : h.nreal;
@@ -116,10 +119,34 @@ __global__ void __launch_bounds__(512, CPLX ? 2 : 1) multi_kernel(const unsigned
   const int64_t per_tile = (int64_t)blockDim.x * M * UNR;
   if (h.tile_matrices != per_tile) return;   // launched with another shape than planned
   auto *redo = reinterpret_cast<unsigned long long *>(const_cast<unsigned char *>(plan) + kRedoOffset);
-  int bi = CPLX ? h.nreal : 0;   // batch of the current tile; tiles only increase
+  // The record of the block's current batch, in shared memory: the threads
+  // read its pointers where they use them instead of holding all of them in
+  // registers across the method.  Every thread of the block walks the same
+  // tiles, so the batch changes for all of them at once (uniform barriers).
+  __shared__ MultiBatch sb;
+  static_assert(sizeof(MultiBatch) % 8 == 0 && sizeof(MultiBatch) / 8 <= 32, "record copy");
+  const int b_begin = CPLX ? h.nreal : 0;
+  int bi = b_begin;   // batch of the current tile; a block's tiles only increase
+  int cur = -1;
   for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    if (cur < 0) {   // the block's first tile: the last batch with tile0 <= t
+      int lo = b_begin, hi = b_end - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (batches[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+      }
+      bi = lo;
+    }
     while (bi + 1 < b_end && batches[bi + 1].tile0 <= t) ++bi;
-    const MultiBatch &b = batches[bi];
+    if (bi != cur) {
+      __syncthreads();            // the previous record is no longer read
+      if (threadIdx.x < sizeof(MultiBatch) / 8)
+        reinterpret_cast<uint64_t *>(&sb)[threadIdx.x] =
+            reinterpret_cast<const uint64_t *>(&batches[bi])[threadIdx.x];
+      __syncthreads();
+      cur = bi;
+    }
+    const MultiBatch &b = sb;
     const int64_t base = (t - b.tile0) * per_tile;
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
@@ -163,6 +190,11 @@ static MultiKernel pick_multi(int mpt, int unroll) {
 }  // namespace svd2
 
 using namespace svd2;
+
+// Tile counts of the plans prepared in this process (real, complex), keyed by
+// the plan's device address: grid 0 launches one block per tile.
+static std::mutex g_tiles_mu;
+static std::unordered_map<const void *, std::pair<int64_t, int64_t>> g_tiles;
 
 extern "C" size_t svd2_multi_plan_bytes(int32_t nbatch) {
   if (nbatch < 0) return 0;
@@ -232,11 +264,24 @@ extern "C" int svd2_multi_prepare(const svd2_batch_desc *descs, int32_t nbatch, 
   delete[] host;
   if (e != cudaSuccess) return record_cuda_error(e);
   if (total_tiles) *total_tiles = tiles_of[0] + tiles_of[1];
+  {
+    std::lock_guard<std::mutex> g(g_tiles_mu);
+    g_tiles[plan] = {tiles_of[0], tiles_of[1]};
+  }
   return SVD2_OK;
 }
 
-static int multi_grid(MultiKernel k, int block, int grid, int *out) {
-  if (grid == 0) {
+// Blocks of one kind's launch.  grid > 0: that many blocks walking the tiles
+// round-robin.  grid 0: one block per tile when the plan's tile count is
+// known here (measured fastest on GB300: the method's long unrolled body
+// stays in the instruction cache while the warps of young blocks run
+// together, where those of long-lived blocks drift apart and stall on
+// instruction fetch), otherwise one resident wave.
+static int multi_grid(MultiKernel k, int block, int grid, int64_t tiles, int *out) {
+  if (grid == 0 && tiles >= 0) {
+    const int64_t g = tiles > 0 ? tiles : 1;
+    grid = (int)(g < 0x7fffffffLL ? g : 0x7fffffffLL);
+  } else if (grid == 0) {
     int resident = 0;
     SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, block, 0));
     grid = sm_count() * (resident > 0 ? resident : 1);
@@ -250,9 +295,18 @@ static int multi_launch(const void *plan, int block, int mpt, int unroll, int gr
                         cudaStream_t st) {
   const MultiKernel kr = pick_multi<false>(mpt, unroll), kz = pick_multi<true>(mpt, unroll);
   if (!kr || !kz || block < 32 || block > 512 || block % 32 || grid < 0) return SVD2_EINVAL;
+  int64_t tr = -1, tz = -1;
+  {
+    std::lock_guard<std::mutex> g(g_tiles_mu);
+    auto it = g_tiles.find(plan);
+    if (it != g_tiles.end()) {
+      tr = it->second.first;
+      tz = it->second.second;
+    }
+  }
   int gr = 0, gz = 0;
-  int rc = multi_grid(kr, block, grid, &gr);
-  if (rc == SVD2_OK) rc = multi_grid(kz, block, grid, &gz);
+  int rc = multi_grid(kr, block, grid, tr, &gr);
+  if (rc == SVD2_OK) rc = multi_grid(kz, block, grid, tz, &gz);
   if (rc != SVD2_OK) return rc;
   const auto *pl = static_cast<const unsigned char *>(plan);
   if (kHotFlags<double>)
