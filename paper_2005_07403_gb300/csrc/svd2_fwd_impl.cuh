@@ -42,6 +42,9 @@ constexpr int32_t kRedoS = INT32_MIN;
 // FP32 form with re-run: the single-precision results stand but the
 // double-precision re-run left its fast domain.
 constexpr int32_t kRedoRerun = INT32_MIN + 1;
+// FP32 form with re-run, first pass: the matrix asks for the re-run (its
+// single-precision sigma' satisfy sigma'_min < 2^tau sigma'_max).
+constexpr int32_t kRerunMark = INT32_MIN + 2;
 
 // Optional back-scaling of Fig. 1: Sigma = 2^-s Sigma' (correctly rounded,
 // may overflow or underflow), then s = 0.
@@ -112,7 +115,10 @@ __device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u
 // M matrices from k0 with the batch arithmetic HotAr, stored with vector
 // stores; a matrix the fast arithmetic cannot finish gets s = kRedoS and
 // raises p.redo.
-template <typename T, bool CPLX, int M, bool VALS = false>
+// MARK (first pass of the FP32 form with re-run): a matrix whose
+// single-precision sigma' ask for the double-precision re-run gets
+// s = kRerunMark.
+template <typename T, bool CPLX, int M, bool VALS = false, bool MARK = false>
 __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p, int64_t k0,
                                               const T (&in)[CPLX ? 8 : 4][M]) {
   constexpr int NA = CPLX ? 8 : 4;
@@ -126,8 +132,10 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
     HotAr<T, CPLX> ar;
     svd2_one<T, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
+    bool mark = false;
+    if constexpr (MARK) mark = sn[m] < fp<T>::mul(p.tau, sx[m]);
     if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
-    so[m] = ar.bad ? kRedoS : so[m];
+    so[m] = ar.bad ? kRedoS : mark ? kRerunMark : so[m];
     bad |= ar.bad;
 #pragma unroll
     for (int e = 0; e < NA; ++e) {
@@ -175,7 +183,7 @@ inline unsigned fix_grid(int64_t n) {
 // registers for full occupancy measured no faster).
 template <typename T, bool CPLX> constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 1;
 
-template <typename T, bool CPLX, int M, int UNR, bool VALS = false>
+template <typename T, bool CPLX, int M, int UNR, bool VALS = false, bool MARK = false>
 __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
     fwd_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
       const int64_t g = g0 + r * stride;
-      if (g < ngroups) process_group<T, CPLX, M, VALS>(p, g * M, in[r]);
+      if (g < ngroups) process_group<T, CPLX, M, VALS, MARK>(p, g * M, in[r]);
     }
   }
   // the n mod M tail, one matrix per thread
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
     T in1[NA][1];
 #pragma unroll
     for (int e = 0; e < NA; ++e) in1[e][0] = p.a[e][k];
-    process_group<T, CPLX, 1, VALS>(p, k, in1);
+    process_group<T, CPLX, 1, VALS, MARK>(p, k, in1);
   }
 }
 

@@ -1,31 +1,35 @@
 // FP32 form with FP64 re-run: svd2_batch_s_rerun / svd2_batch_c_rerun.
 //
-// Each block takes tiles of consecutive matrices; for a tile it first runs the
-// single-precision method (Sec. 1, Sec. 7) on every matrix and flags each
-// matrix whose scaled singular values satisfy sigma'_min < 2^tau sigma'_max
-// (compared in float; the product by the power of two is exact), queueing its
-// index and input elements in shared memory.  Once the queue holds a block's
-// worth (and at the end), the whole block re-runs the queued matrices, on
-// full warps, with the double-precision method on the exactly widened input,
-// and overwrites their outputs with the double results rounded to float,
-// sigma' brought to the float run's scale: sigma'_32 = RN32(sigma'_64
-// 2^(s32 - s64)).  The re-run reads its inputs from shared memory; its
-// scattered stores rewrite lines the block wrote a few tiles earlier, part of
-// which have left L2 by then (measured: +74% DRAM reads, +27% writes over
-// the algorithmic bytes).  The number of re-run matrices is accumulated in
-// the workspace.  A second kernel, the fix-up pass, finishes the matrices the
-// fast arithmetic of either precision could not (reads one word otherwise).
+// Four launches on the caller's stream:
+//  1. the single-precision batch kernel (fwd_kernel, as svd2_batch_s / _c, Sec.
+//     1, Sec. 7) over all n matrices, which also marks (s = kRerunMark) every
+//     matrix whose scaled singular values satisfy sigma'_min < 2^tau sigma'_max
+//     (compared in float; the product by the power of two is exact);
+//  2. compact_kernel: the marked indices, in increasing order within each
+//     chunk, appended to a list in the workspace (reads s, 4 bytes a matrix);
+//  3. list_rerun_kernel: every listed matrix decomposed again, one per thread
+//     on full warps, by the double-precision method on the exactly widened
+//     input, its outputs replaced by the double results rounded to float with
+//     sigma' brought to the float run's scale: sigma'_32 = RN32(sigma'_64
+//     2^(s32 - s64));
+//  4. the fix-up pass, which finishes the matrices the fast single-precision
+//     arithmetic could not (reads one word otherwise).
+// Passes 1 and 3 are separate kernels so that each gets its own register
+// budget and occupancy: the single-precision kernel is bound by HBM, the
+// re-run by the FP64 and integer pipes.  The re-run's gathers and scattered
+// 4-byte stores touch about 0.7 sectors per array and re-run matrix (one in
+// ten matrices at the 2^-8 threshold on the ill-conditioned mix).
 #include "svd2_fwd_impl.cuh"
 
 namespace svd2 {
 
 // Workspace layout: [0] re-run count of the call (uint64), [8] the fix-up
-// flag of the call (uint64).  The size formula (256 bytes plus 4 per matrix)
-// also leaves room for an index list, which this form keeps in shared memory.
+// flag of the call (uint64), [16] the list length of the current chunk
+// (uint64); from byte 256 the index list, 4 bytes per matrix of a chunk.
 constexpr size_t kListOffset = 256;
 constexpr int64_t kChunk = int64_t(1) << 31;
 
-// Re-run of one queued matrix in double precision with the arithmetic policy
+// Re-run of one matrix in double precision with the arithmetic policy
 // Ar; float outputs u, v, sigma' stored (s is left to the caller).  Returns the
 // final s of the matrix (the float run's exponent, or 0 after back-scaling).
 // With FastAr, ar.bad set means the stored outputs are unspecified.
@@ -64,133 +68,92 @@ __device__ __forceinline__ int32_t rerun_one(Ar &ar, const FwdArgs<float, CPLX ?
   return s32;
 }
 
-// Queue matrix k (index and input elements) for the double-precision re-run.
-template <int NA>
-__device__ __forceinline__ void enqueue(uint32_t k, const float *a, uint32_t *q_idx, float *q_a,
-                                        int qcap, int *q_n) {
-  const int pos = atomicAdd(q_n, 1);      // shared memory; pos < qcap (one slot per matrix)
-  q_idx[pos] = k;
-#pragma unroll
-  for (int e = 0; e < NA; ++e) q_a[e * qcap + pos] = a[e];
-}
+// Arithmetic of the double-precision re-run: the general arithmetic, whose
+// division and square root run on the integer pipe, so that the FP64 pipe (2
+// results per clock per SM) executes only the method's own operations;
+// measured faster than the hardware division and square root here.
+using RerunAr = ExactAr<double>;
 
-// The single-precision method on M matrices from k0, queueing the matrices
-// whose sigma' ask for the re-run; a matrix the fast arithmetic cannot finish
-// gets s = kRedoS (the fix-up kernel then decides its re-run).
-template <bool CPLX, int M>
-__device__ __forceinline__ void fp32_group(const FwdArgs<float, CPLX ? 8 : 4> &p, int64_t k0,
-                                           const float (&in)[CPLX ? 8 : 4][M], uint32_t *q_idx,
-                                           float *q_a, int qcap, int *q_n) {
-  constexpr int NA = CPLX ? 8 : 4;
-  float uo[NA][M], vo[NA][M], sx[M], sn[M];
-  int32_t so[M];
-  unsigned bad = 0;
+// Pass 2: the indices k with s[k] == kRerunMark, in increasing order within
+// each chunk of 16 * blockDim.x matrices (one warp-scan and one block-scan of
+// the per-thread counts), each chunk appended to the list with one atomic on
+// its length.  vec: s is 16-byte aligned (vector loads).
+__global__ void __launch_bounds__(256) compact_kernel(const int32_t *s, int64_t n, uint32_t *list,
+                                                      unsigned long long *len, bool vec) {
+  __shared__ int warp_sum[8];
+  __shared__ unsigned long long base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t chunk = 16 * (int64_t)blockDim.x;
+  for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < n; c0 += (int64_t)gridDim.x * chunk) {
+    const int64_t k0 = c0 + 16 * (int64_t)threadIdx.x;
+    unsigned bits = 0;
+    if (vec && k0 + 16 <= n) {
 #pragma unroll
-  for (int m = 0; m < M; ++m) {
-    float a[NA], u[NA], v[NA];
-#pragma unroll
-    for (int e = 0; e < NA; ++e) a[e] = in[e][m];
-    HotAr<float, CPLX> ar;
-    svd2_one<float, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
-    if (!ar.bad && sn[m] < fp<float>::mul(p.tau, sx[m]))
-      enqueue<NA>((uint32_t)(k0 + m), a, q_idx, q_a, qcap, q_n);
-    if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
-    so[m] = ar.bad ? kRedoS : so[m];
-    bad |= ar.bad;
-#pragma unroll
-    for (int e = 0; e < NA; ++e) {
-      uo[e][m] = u[e];
-      vo[e][m] = v[e];
+      for (int q = 0; q < 4; ++q) {
+        const int4 w = __ldcs(reinterpret_cast<const int4 *>(s + k0) + q);
+        bits |= (unsigned)(w.x == kRerunMark) << (4 * q) | (unsigned)(w.y == kRerunMark) << (4 * q + 1) |
+                (unsigned)(w.z == kRerunMark) << (4 * q + 2) | (unsigned)(w.w == kRerunMark) << (4 * q + 3);
+      }
+    } else {
+      for (int j = 0; j < 16 && k0 + j < n; ++j) bits |= (unsigned)(s[k0 + j] == kRerunMark) << j;
     }
+    const int cnt = __popc(bits);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int x = warp_sum[w];
+        warp_sum[w] = tot;
+        tot += x;
+      }
+      base = tot ? atomicAdd(len, (unsigned long long)tot) : 0;
+    }
+    __syncthreads();
+    uint64_t pos = base + warp_sum[warp] + (incl - cnt);
+    while (bits) {
+      const int j = __ffs(bits) - 1;
+      bits &= bits - 1;
+      list[pos++] = (uint32_t)(k0 + j);
+    }
+    __syncthreads();
   }
-#pragma unroll
-  for (int e = 0; e < NA; ++e) store_vec<float, M>(p.u[e] + k0, uo[e]);
-#pragma unroll
-  for (int e = 0; e < NA; ++e) store_vec<float, M>(p.v[e] + k0, vo[e]);
-  store_vec<float, M>(p.smax + k0, sx);
-  store_vec<float, M>(p.smin + k0, sn);
-  store_vec<int32_t, M>(p.s + k0, so);
-  if (bad) *p.redo = 1;
 }
 
-// Drain the block's queue -- every queued matrix re-run in double precision --
-// once it holds at least `min_fill` entries (0: whatever it holds).  Called by
-// every thread of the block; the decision is uniform.
+// Pass 3: the listed matrices re-run in double precision, one per thread
+// (full warps), outputs and s stored over the single-precision ones; the list
+// length is read on the device, so the grid is one resident wave.
 template <bool CPLX>
-__device__ __forceinline__ void drain(const FwdArgs<float, CPLX ? 8 : 4> &p, const uint32_t *q_idx,
-                                      const float *q_a, int qcap, int *q_n, int min_fill) {
+__global__ void __launch_bounds__(512, 2)
+    list_rerun_kernel(const __grid_constant__ FwdArgs<float, CPLX ? 8 : 4> p, const uint32_t *list,
+                      const unsigned long long *len) {
   constexpr int NA = CPLX ? 8 : 4;
-  __syncthreads();
-  const int qn = *q_n;
-  if (qn == 0 || qn < min_fill) return;
-  for (int i = threadIdx.x; i < qn; i += blockDim.x) {
+  const int64_t L = (int64_t)*len;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += step) {
+    const uint32_t k = list[i];
     float a[NA];
 #pragma unroll
-    for (int e = 0; e < NA; ++e) a[e] = q_a[e * qcap + i];
-    FastAr<double> ar;
-    rerun_one<CPLX>(ar, p, q_idx[i], a);
+    for (int e = 0; e < NA; ++e) a[e] = p.a[e][k];
+    RerunAr ar;
+    const int32_t s32 = rerun_one<CPLX>(ar, p, k, a);
     if (ar.bad) {                       // the fix-up kernel re-runs it exactly
-      p.s[q_idx[i]] = kRedoRerun;
+      p.s[k] = kRedoRerun;
       *p.redo = 1;
+    } else {
+      p.s[k] = s32;
     }
   }
-  if (threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)qn);
-  __syncthreads();
-  if (threadIdx.x == 0) *q_n = 0;
-  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)L);
 }
 
-// Tiles of blockDim * M * UNR matrices; every thread of a block runs the same
-// number of tile iterations, so the barriers of drain() are uniform.  The
-// queue holds one tile plus one block of matrices and is drained when it has
-// a block's worth (full warps in the double-precision pass), and at the end.
-template <bool CPLX, int M, int UNR>
-__global__ void __launch_bounds__(512)
-    fused_rerun_kernel(const __grid_constant__ FwdArgs<float, CPLX ? 8 : 4> p) {
-  constexpr int NA = CPLX ? 8 : 4;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int qcap = blockDim.x * (M * UNR + 1);
-  int *q_n = reinterpret_cast<int *>(smem);
-  uint32_t *q_idx = reinterpret_cast<uint32_t *>(smem + 16);
-  float *q_a = reinterpret_cast<float *>(smem + 16 + (size_t)qcap * sizeof(uint32_t));
-  if (threadIdx.x == 0) *q_n = 0;
-  __syncthreads();
-  const int64_t ngroups = p.n / M;
-  const int64_t per_tile = (int64_t)blockDim.x * UNR;      // groups per tile
-  const int64_t ntiles = (ngroups + per_tile - 1) / per_tile;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    float in[UNR][NA][M];
-#pragma unroll
-    for (int r = 0; r < UNR; ++r) {
-      const int64_t g = t * per_tile + (int64_t)r * blockDim.x + threadIdx.x;
-      if (g < ngroups) {
-#pragma unroll
-        for (int e = 0; e < NA; ++e) load_vec<float, M>(p.a[e] + g * M, in[r][e]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < UNR; ++r) {
-      const int64_t g = t * per_tile + (int64_t)r * blockDim.x + threadIdx.x;
-      if (g < ngroups) fp32_group<CPLX, M>(p, g * M, in[r], q_idx, q_a, qcap, q_n);
-    }
-    drain<CPLX>(p, q_idx, q_a, qcap, q_n, blockDim.x);
-  }
-  // the n mod M tail, one matrix per thread of block 0
-  const int64_t tail = p.n - ngroups * M;
-  if (blockIdx.x == 0 && tail > 0 && threadIdx.x < tail) {
-    const int64_t k = ngroups * M + threadIdx.x;
-    float in1[NA][1];
-#pragma unroll
-    for (int e = 0; e < NA; ++e) in1[e][0] = p.a[e][k];
-    fp32_group<CPLX, 1>(p, k, in1, q_idx, q_a, qcap, q_n);
-  }
-  drain<CPLX>(p, q_idx, q_a, qcap, q_n, 0);
-}
-
-using FusedKernel4 = void (*)(const FwdArgs<float, 4>);
-using FusedKernel8 = void (*)(const FwdArgs<float, 8>);
-
-// Fix-up pass of the re-run form (same stream, after the fused kernel): s =
+// Fix-up pass of the re-run form (same stream, after the re-run pass): s =
 // kRedoS -- the single-precision method with the general arithmetic, then the
 // re-run test and, if it asks, the double-precision re-run (counted);
 // s = kRedoRerun -- the double-precision re-run with the general arithmetic
@@ -221,10 +184,12 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Pass 1 kernels: fwd_kernel with the re-run marks, in the launch shapes of
+// the plain single-precision form.
 template <bool CPLX>
-static auto pick_fused(int mpt, int unroll) -> void (*)(const FwdArgs<float, CPLX ? 8 : 4>) {
+static FwdKernel<float, CPLX> pick_mark(int mpt, int unroll) {
 #define SVD2_PICK(M_, U_) \
-  if (mpt == M_ && unroll == U_) return fused_rerun_kernel<CPLX, M_, U_>;
+  if (mpt == M_ && unroll == U_) return fwd_kernel<float, CPLX, M_, U_, false, true>;
   SVD2_PICK(1, 1) SVD2_PICK(1, 2) SVD2_PICK(2, 1) SVD2_PICK(2, 2) SVD2_PICK(4, 1) SVD2_PICK(4, 2)
 #undef SVD2_PICK
   return nullptr;
@@ -241,7 +206,7 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
     return SVD2_EINVAL;
   if (!A || !U || !V || !smax || !smin || !s) return SVD2_EINVAL;
   auto *count = static_cast<unsigned long long *>(workspace);
-  SVD2_CUDA_TRY(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), stream));
+  auto *list = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(workspace) + kListOffset);
   Launch L = get_launch(op);
   bool vec_ok = aligned(smax, 16) && aligned(smin, 16) && aligned(s, 16);
   for (int e = 0; e < NA; ++e) {
@@ -249,15 +214,15 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
     vec_ok = vec_ok && aligned(A[e], 16) && aligned(U[e], 16) && aligned(V[e], 16);
   }
   if (!vec_ok) L.mpt = 1;
-  auto k = pick_fused<CPLX>(L.mpt, L.unroll);
+  auto k = pick_mark<CPLX>(L.mpt, L.unroll);
   if (!k) return SVD2_EINVAL;
-  const size_t qcap = (size_t)L.block * (L.mpt * L.unroll + 1);
-  const size_t shmem = 16 + qcap * sizeof(uint32_t) + qcap * NA * sizeof(float);
-  SVD2_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
-  int resident = 0;
-  SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, L.block, shmem));
+  int resident = 0, resident2 = 0;
+  SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, L.block, 0));
+  SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident2, list_rerun_kernel<CPLX>, 512, 0));
+  SVD2_CUDA_TRY(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), stream));
   for (int64_t base = 0; base < n; base += kChunk) {
     const int64_t m = (n - base < kChunk) ? (n - base) : kChunk;
+    SVD2_CUDA_TRY(cudaMemsetAsync(count + 2, 0, sizeof(unsigned long long), stream));
     FwdArgs<float, NA> p{};
     for (int e = 0; e < NA; ++e) {
       p.a[e] = A[e] + base;
@@ -273,11 +238,18 @@ static int rerun_form(int op, int64_t n, const float *const *A, float *const *U,
     p.count = count;
     p.redo = count + 1;
     p.stride = 1;
-    const int64_t tiles = (m / L.mpt + (int64_t)L.block * L.unroll - 1) / ((int64_t)L.block * L.unroll);
-    const int64_t cap = (int64_t)sm_count() * (resident > 0 ? resident : 1) * (L.waves > 0 ? L.waves : 1 << 20);
-    int64_t grid = tiles < 1 ? 1 : tiles;
-    if (grid > cap) grid = cap;
-    k<<<(unsigned)grid, L.block, shmem, stream>>>(p);
+    const int64_t groups = m / L.mpt, tail = m % L.mpt;
+    const int64_t loops = (groups + L.unroll - 1) / L.unroll;
+    const int64_t grid = grid_for(loops > tail ? loops : tail, L, resident);
+    k<<<(unsigned)grid, L.block, 0, stream>>>(p);
+    SVD2_CUDA_TRY(cudaGetLastError());
+    const int64_t chunks = (m + 4095) / 4096;
+    const int64_t cgrid = chunks < (int64_t)sm_count() * 8 ? chunks : (int64_t)sm_count() * 8;
+    compact_kernel<<<(unsigned)cgrid, 256, 0, stream>>>(p.s, m, list, count + 2, aligned(p.s, 16));
+    SVD2_CUDA_TRY(cudaGetLastError());
+    const int64_t want = (m + 511) / 512;
+    const int64_t cap = (int64_t)sm_count() * (resident2 > 0 ? resident2 : 1);
+    list_rerun_kernel<CPLX><<<(unsigned)(want < cap ? want : cap), 512, 0, stream>>>(p, list, count + 2);
     SVD2_CUDA_TRY(cudaGetLastError());
     rerun_fix_kernel<CPLX><<<fix_grid(m), 256, 0, stream>>>(p);
     SVD2_CUDA_TRY(cudaGetLastError());

@@ -1,5 +1,6 @@
-"""The persistent multi-batch launch (svd2_multi_*), its CUDA graph, and the
-autotuners, against the oracle batch by batch (bit for bit)."""
+"""The multi-batch launch (svd2_multi_*: one block per tile by default, or a
+persistent grid), its CUDA graph, and the autotuners, against the oracle
+batch by batch (bit for bit)."""
 import numpy as np
 import pytest
 import torch
@@ -40,6 +41,16 @@ def test_multi_matches_oracle_per_batch(shape):
     mb = S.MultiBatch([torch.from_numpy(A).cuda() for A in hosts], *shape)
     mb.run()
     _check_all(mb, hosts, str(shape))
+
+
+@pytest.mark.parametrize("grid", [1, 7, 304, 100000])
+def test_multi_explicit_grids_match(grid):
+    """A persistent grid (one block, a few, one resident wave) and a grid with
+    more blocks than tiles give the same results as one block per tile."""
+    hosts = _batches(30, 5, hi=6000)
+    mb = S.MultiBatch([torch.from_numpy(A).cuda() for A in hosts], 256, 1, 1)
+    mb.run(grid=grid)
+    _check_all(mb, hosts, f"grid {grid}")
 
 
 def test_multi_graph_replay_follows_data():
