@@ -43,9 +43,15 @@ constexpr uint64_t kAbs = 0x7fffffffffffffffull;
 constexpr uint64_t kFrac = 0x000fffffffffffffull;
 constexpr uint64_t kImpl = 0x0010000000000000ull;
 
+// The bit pattern of x.  On the device it passes through an opaque register
+// move: written as a plain reinterpretation, the compiler turns tests on the
+// pattern (zero, normal, finite) back into floating-point comparisons, which
+// run on the FP64 pipe at 1/64 of the integer rate.
 SFP_FN uint64_t dbits(double x) {
 #if defined(__CUDA_ARCH__)
-  return (uint64_t)__double_as_longlong(x);
+  uint64_t u;
+  asm("mov.b64 %0, %1;" : "=l"(u) : "d"(x));
+  return u;
 #else
   uint64_t u;
   std::memcpy(&u, &x, 8);
