@@ -382,8 +382,11 @@ int svd2_get_launch(int op, int *block, int *mpt, int *unroll, int *waves);
  * to nearest even (on GB300 the hardware IEEE double division and square root
  * take ~10 slots each of the narrow FP64 pipe).  For i < n this writes
  * lib[i] = the library's result and hw[i] = the hardware instruction's
- * (op 0: x[i] / y[i]; op 1: sqrt(x[i]); y unused for op 1).  All pointers are
- * device arrays of n doubles.  The two must agree bit for bit.
+ * (op 0: x[i] / y[i]; op 1: sqrt(x[i]); op 2: x[i] rounded to float, stored
+ * widened exactly; op 3: the float whose bit pattern is the low 32 bits of
+ * x[i], widened to double -- the conversions of the FP32 form's FP64 re-run;
+ * y unused for ops 1-3).  All pointers are device arrays of n doubles.  The
+ * two must agree bit for bit (NaNs: any NaN).
  */
 int svd2_arith_check(int op, int64_t n, const double *x, const double *y, double *lib,
                      double *hw, svd2_stream_t stream);

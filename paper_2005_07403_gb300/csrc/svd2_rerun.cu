@@ -41,7 +41,7 @@ __device__ __forceinline__ int32_t rerun_one(Ar &ar, const FwdArgs<float, CPLX ?
   unsigned mx = 0;
 #pragma unroll
   for (int e = 0; e < NA; ++e) {
-    ad[e] = (double)a[e];
+    ad[e] = sfp::f2d(a[e]);   // float <-> double on the integer pipe
     const unsigned b = fp<float>::bits(a[e]) & fp<float>::kAbs;
     mx = b > mx ? b : mx;
   }
@@ -49,8 +49,8 @@ __device__ __forceinline__ int32_t rerun_one(Ar &ar, const FwdArgs<float, CPLX ?
   double u[NA], v[NA], sx, sn;
   int32_t s64;
   svd2_one<double, CPLX>(ar, ad, u, v, sx, sn, s64);
-  float fx = __double2float_rn(ar.scale(sx, s32 - s64));
-  float fn = __double2float_rn(ar.scale(sn, s32 - s64));
+  float fx = sfp::d2f(ar.scale(sx, s32 - s64));
+  float fn = sfp::d2f(ar.scale(sn, s32 - s64));
   if (p.flags & SVD2_BACKSCALE) {
     if (s32 != kZeroS) {
       fx = ar.template scale_as<float>(fx, -s32);
@@ -60,8 +60,8 @@ __device__ __forceinline__ int32_t rerun_one(Ar &ar, const FwdArgs<float, CPLX ?
   }
 #pragma unroll
   for (int e = 0; e < NA; ++e) {
-    p.u[e][k] = __double2float_rn(u[e]);
-    p.v[e][k] = __double2float_rn(v[e]);
+    p.u[e][k] = sfp::d2f(u[e]);
+    p.v[e][k] = sfp::d2f(v[e]);
   }
   p.smax[k] = fx;
   p.smin[k] = fn;

@@ -1,6 +1,7 @@
 // svd2_arith_check: the library's double division and square root (computed on
-// the integer and FP32 pipes, svd2_softfp.cuh) next to the hardware's IEEE
-// instructions, element by element, for testing on the device.
+// the integer and FP32 pipes, svd2_softfp.cuh) and its float <-> double
+// conversions (integer pipe) next to the hardware's IEEE instructions, element
+// by element, for testing on the device.
 #include "svd2_common.cuh"
 #include "svd2_softfp.cuh"
 
@@ -15,9 +16,16 @@ __global__ void arith_check_kernel(int op, int64_t n, const double *x, const dou
       const double b = y[i];
       lib[i] = svd2::sfp::div_rn(a, b);
       hw[i] = __ddiv_rn(a, b);
-    } else {
+    } else if (op == 1) {
       lib[i] = svd2::sfp::sqrt_rn(a);
       hw[i] = __dsqrt_rn(a);
+    } else if (op == 2) {
+      lib[i] = (double)svd2::sfp::d2f(a);
+      hw[i] = (double)__double2float_rn(a);
+    } else {
+      const float f = __uint_as_float((unsigned)__double2loint(a));
+      lib[i] = svd2::sfp::f2d(f);
+      hw[i] = (double)f;
     }
   }
 }
@@ -26,7 +34,7 @@ __global__ void arith_check_kernel(int op, int64_t n, const double *x, const dou
 
 extern "C" int svd2_arith_check(int op, int64_t n, const double *x, const double *y, double *lib,
                                 double *hw, svd2_stream_t stream) {
-  if (op != 0 && op != 1) return SVD2_EINVAL;
+  if (op < 0 || op > 3) return SVD2_EINVAL;
   if (n < 0) return SVD2_EINVAL;
   if (n == 0) return SVD2_OK;
   if (!x || !lib || !hw || (op == 0 && !y)) return SVD2_EINVAL;

@@ -1,5 +1,6 @@
 // Correctly rounded (round to nearest, ties to even) IEEE double division and
-// square root computed on the integer and FP32 pipes.
+// square root computed on the integer and FP32 pipes, and the conversions
+// between float and double on the integer pipe (end of file).
 //
 // On GB300 the FP64 pipe retires 2 lanes per clock per SM, and the hardware
 // IEEE double division and square root each take about ten of its slots, while
@@ -293,6 +294,41 @@ SFP_FN double sqrt_rn(double x) {
   const uint64_t ux = dbits(x);
   if (!((uint32_t)(ux >> 52) - 1u < 2046u)) return hw_sqrt(x);   // +-0, subnormal, negative, inf, NaN
   return sqrt_core(ux);
+}
+
+// Conversions between float and double on the integer pipe (the conversion
+// instruction runs on the FP64 pipe).
+// f2d: exact widening; normal numbers and zeros here, the instruction for
+// subnormal, infinite and NaN inputs.
+SFP_FN double f2d(float x) {
+  const uint32_t b = fbits(x);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+  if (e - 1u < 254u)
+    return dval(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29));
+  if ((b & 0x7fffffffu) == 0) return dval(sign);
+  return (double)x;
+}
+// d2f: round to nearest float, ties to even, for results in the normal float
+// range (a carry out of the significand moves to the next binade, and past
+// FLT_MAX to infinity, as rounding to nearest does) and for zeros; the
+// instruction for subnormal float results, infinities and NaNs.
+SFP_FN float d2f(double x) {
+  const uint64_t u = dbits(x);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const uint32_t ef = ((hi >> 20) & 0x7ffu) - 896u;      // float biased exponent
+  if (ef - 1u < 254u) {
+    uint32_t r = (ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;                 // the 29 dropped bits
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+    return fval((hi & 0x80000000u) | r);
+  }
+  if (((hi & 0x7fffffffu) | lo) == 0) return fval(hi & 0x80000000u);
+#if defined(__CUDA_ARCH__)
+  return __double2float_rn(x);
+#else
+  return (float)x;
+#endif
 }
 
 }  // namespace sfp

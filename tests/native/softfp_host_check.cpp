@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 
 #include "svd2_softfp.cuh"
 
@@ -42,6 +43,28 @@ static void chk_sqrt(double x) {
   }
 }
 
+static void chk_d2f(double x) {
+  const float r = svd2::sfp::d2f(x), h = (float)x;
+  ++checked;
+  uint32_t br, bh;
+  std::memcpy(&br, &r, 4);
+  std::memcpy(&bh, &h, 4);
+  if (br != bh && !(std::isnan(r) && std::isnan(h))) {
+    if (bad < 10) std::printf("d2f mismatch x=%a soft=%a hw=%a\n", x, (double)r, (double)h);
+    ++bad;
+  }
+}
+static void chk_f2d(uint32_t b) {
+  float f;
+  std::memcpy(&f, &b, 4);
+  const double r = svd2::sfp::f2d(f), h = (double)f;
+  ++checked;
+  if (dbits(r) != dbits(h) && !(std::isnan(r) && std::isnan(h))) {
+    if (bad < 10) std::printf("f2d mismatch x=%a soft=%a hw=%a\n", (double)f, r, h);
+    ++bad;
+  }
+}
+
 // a double with the given biased exponent and mantissa bits
 static double mk(uint64_t sign, uint64_t bexp, uint64_t frac) {
   return dval((sign << 63) | ((bexp & 0x7ff) << 52) | (frac & 0xfffffffffffffull));
@@ -54,7 +77,27 @@ int main(int argc, char **argv) {
                                0x8000000000000ull, 0x7ffffffffffffull, 0x0000000000001ull,
                                0xaaaaaaaaaaaaaull, 0x5555555555555ull, 0xfffff00000000ull,
                                0x00000fffffffful, 0x1000000000000ull};
+  // conversion boundaries: FLT_MAX and the tie above it (rounds to infinity),
+  // the smallest normal float and the binade below it, zeros, infinities, NaN
+  for (int sg = 0; sg < 2; ++sg) {
+    for (uint64_t fr : {0xfffffe0000000ull, 0xfffffefffffffull, 0xffffff0000000ull,
+                        0xfffffffffffffull, 0ull, 0x0000010000000ull, 0x0000001ull})
+      for (uint64_t e : {1150ull, 1151ull, 1152ull, 895ull, 896ull, 897ull, 0ull, 2047ull})
+        chk_d2f(mk(sg, e, fr));
+    for (uint32_t b : {0u, 1u, 0x7fffffu, 0x800000u, 0x7f7fffffu, 0x7f800000u, 0x7fc00000u,
+                       0x7f800001u, 0x3f800000u})
+      chk_f2d(b | (sg ? 0x80000000u : 0u));
+  }
   for (long long i = 0; i < n; ++i) {
+    // conversions: any float pattern; doubles around the float range (float
+    // subnormal results, overflow), with the 29 dropped bits random, exactly
+    // half an ulp (ties), or half an ulp +-1
+    chk_f2d((uint32_t)sm64(s));
+    chk_d2f(dval(sm64(s)));
+    const uint64_t ec = 896 - 26 + sm64(s) % 284, fc = sm64(s);
+    const uint64_t drop[] = {fc & 0x1fffffffull, 0x10000000ull, 0x0fffffffull, 0x10000001ull, 0};
+    const uint64_t fr = (fc & ~0x1fffffffull) | drop[sm64(s) % 5];
+    chk_d2f(mk(sm64(s) & 1, ec, fr));
     // uniform random bit patterns (any class: normal, subnormal, zero, inf, NaN)
     chk_div(dval(sm64(s)), dval(sm64(s)));
     chk_sqrt(dval(sm64(s)));

@@ -67,3 +67,28 @@ def test_sqrt_matches_hardware(cls):
     lib, hw = S.arith_check("sqrt", x)
     torch.cuda.synchronize()
     assert _same(lib, hw), cls
+
+
+@pytest.mark.parametrize("cls", ["anybits", "float-range", "ties"])
+def test_rounding_to_float_matches_hardware(cls):
+    """Double -> float on the integer pipe (the FP64 re-run's outputs)."""
+    if cls == "anybits":
+        x = _bits(N, 31).view(torch.float64)
+    else:                          # around the float range: subnormal results, overflow
+        x = _with_exponent(_bits(N, 32), 896 - 26, 896 + 258, 33)
+        if cls == "ties":          # the 29 dropped bits exactly half an ulp, or +-1 from it
+            b = x.view(torch.int64) & ~((1 << 29) - 1)
+            g = torch.Generator(device="cuda").manual_seed(34)
+            d = torch.randint(-1, 2, b.shape, generator=g, device="cuda", dtype=torch.int64)
+            x = (b | ((1 << 28) + d)).view(torch.float64)
+    lib, hw = S.arith_check("d2f", x)
+    torch.cuda.synchronize()
+    assert _same(lib, hw), cls
+
+
+def test_widening_from_float_matches_hardware():
+    """Float -> double on the integer pipe, every class of float pattern."""
+    x = (_bits(N, 41) & 0xFFFFFFFF).view(torch.float64)
+    lib, hw = S.arith_check("f2d", x)
+    torch.cuda.synchronize()
+    assert _same(lib, hw)
