@@ -142,6 +142,32 @@ def real_fp32_illcond(n: int = 2**26, seed: int = SEED_CFG3):
     return np.ascontiguousarray(A.astype(np.float32)), mask
 
 
+def complex_fp32_illcond(n: int = 2**25, seed: int = SEED_CFG3 + 100):
+    """Complex batch for the complex FP32 form with re-run: 90% i.i.d. N(0,1)
+    parts and 10% ill-conditioned D1 R(t1) diag(1, 10^-u) R(t2)^T D2 with
+    D1 = diag(e^(i a1), e^(i a2)), D2 = diag(e^(i b1), e^(i b2)), the phases
+    uniform in [0, 2pi) and t, u drawn as in ``real_fp32_illcond`` (the phase
+    factors are unitary: the singular values are 1 and 10^-u).  Generated in
+    FP64 and rounded to FP32.  Returns (A32 of shape (8, n), is_illcond mask)."""
+    rng = _rng(seed)
+    A = rng.standard_normal((8, n), dtype=np.float64)
+    ni = n // 10
+    idx = rng.permutation(n)[:ni]
+    t1 = rng.uniform(0.0, 2 * np.pi, ni)
+    t2 = rng.uniform(0.0, 2 * np.pi, ni)
+    u = rng.uniform(2.0, 12.0, ni)
+    ph = rng.uniform(0.0, 2 * np.pi, (4, ni))          # a1, a2, b1, b2
+    M = _from_rotations(t1, np.ones(ni), 10.0 ** (-u), t2)   # m11, m21, m12, m22
+    # entry (i, j) of D1 M D2 is e^(i (a_i + b_j)) m_ij
+    for e, (ai, bj) in enumerate(((0, 2), (1, 2), (0, 3), (1, 3))):
+        phase = ph[ai] + ph[bj]
+        A[2 * e, idx] = M[e] * np.cos(phase)
+        A[2 * e + 1, idx] = M[e] * np.sin(phase)
+    mask = np.zeros(n, bool)
+    mask[idx] = True
+    return np.ascontiguousarray(A.astype(np.float32)), mask
+
+
 def kog_batches(seed: int = SEED_CFG4, count: int = 2048, lo_log2: float = 4.0,
                 hi_log2: float = 20.0):
     """Batch shapes of a sequence of Kogbetliantz steps: ``count`` batches with

@@ -40,6 +40,14 @@ def test_rerun_complex_matches_oracle():
     assert cnt == o["count"] > 0
 
 
+def test_rerun_complex_illcond_matches_oracle():
+    A, _ = inputs.complex_fp32_illcond(2**16 + 13, seed=64)
+    g, cnt = run(A, -8)
+    o = oracle.svd2_rerun(A, -8)
+    assert_same(g, o, "c_rerun ill-conditioned")
+    assert cnt == o["count"] > 2**16 // 20
+
+
 def test_rerun_edge_and_backscale():
     A = np.ascontiguousarray(np.concatenate([inputs.edge_real(np.float32),
                                              inputs.random_bits_f32(4096, 4, 62)], axis=1))

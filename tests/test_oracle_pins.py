@@ -466,6 +466,13 @@ def test_generators_shapes_and_classes():
     assert B.shape == (8, 1000) and np.all(np.isfinite(B))
     C, ill = inputs.real_fp32_illcond(1000)
     assert C.dtype == np.float32 and ill.sum() == 100
+    # complex ill-conditioned members: singular values 1 and 10^-u, u in [2, 12]
+    Z, zill = inputs.complex_fp32_illcond(2000, seed=7)
+    assert Z.shape == (8, 2000) and Z.dtype == np.float32 and zill.sum() == 200
+    Zc = Z.astype(np.float64)[0::2] + 1j * Z.astype(np.float64)[1::2]   # a11, a21, a12, a22
+    M = np.stack([np.stack([Zc[0], Zc[2]], -1), np.stack([Zc[1], Zc[3]], -1)], -2)
+    sv = np.linalg.svd(M[zill], compute_uv=False)
+    assert np.abs(sv[:, 0] - 1).max() < 1e-6 and (sv[:, 1] / sv[:, 0]).max() < 0.011
     lens, cplx = inputs.kog_batches()
     assert lens.size == 2048 and lens.min() >= 16 and lens.max() <= 2**20
     assert np.array_equal(inputs.normal_batch(10, 4, 5), inputs.normal_batch(10, 4, 5))
