@@ -629,10 +629,10 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     ms_per_step = ms_max / args.steps
     value = world * n * args.steps / (ms_max / 1e3)
-    # our kernels per call: the FP32 forms run the batch kernel and its fix-up
-    # pass (plus a memset of their flag words), the re-run form also the list
-    # compaction and the re-run pass; the FP64 forms one kernel
-    launches_per_step = 4 if W["form"] == "rerun" else 2 if W["dtype"] == "f32" else 1
+    # our kernels per call: the batch kernel and its fix-up pass (plus a memset
+    # of the flag word); the re-run form also the list compaction and the
+    # re-run pass
+    launches_per_step = 4 if W["form"] == "rerun" else 2
 
     # end to end through the C ABI with host buffers (svd2_batch_host): every
     # step copies A in and every output out through the chunked pipeline

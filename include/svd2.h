@@ -64,6 +64,15 @@ typedef struct CUstream_st *svd2_stream_t;
  * each; smax, smin: n doubles; s: n int32.  Sec. 2 with the real forms of
  * Eq. 10; every step is a correctly rounded IEEE double operation in the
  * paper's order, so the results are those of the step-by-step method.
+ * Every batch form runs as two kernels on the stream: the batch kernel
+ * finishes every matrix whose divisions, square roots and scaling stay in the
+ * normal range on branch-free instruction sequences and marks the others; a
+ * second kernel (which reads one flag word and ends when nothing was marked)
+ * recomputes the marked ones (zero columns, subnormal entries, entries
+ * spanning the exponent range) with the general sequences -- the same
+ * correctly rounded results either way.  Each call takes a 256-byte flag block
+ * from a stream-ordered memory pool that the library creates per device on
+ * first use (it keeps what it allocates until the process exits).
  */
 int svd2_batch_d(int64_t n, const double *const A[4], double *const U[4],
                  double *const V[4], double *smax, double *smin, int32_t *s,
@@ -77,14 +86,7 @@ int svd2_batch_z(int64_t n, const double *const A[8], double *const U[8],
 
 /* Real FP32: the single-precision variant of Sec. 1 and Sec. 7 (FLT_*
  * constants, h = FLT_MAX_EXP - 3 = 125, tan(2 phi) bounded by sqrt(FLT_MAX)).
- * The FP32 forms run as two kernels on the stream: the batch kernel finishes
- * every matrix whose divisions and scaling stay in the normal range on
- * branch-free instruction sequences and marks the others; a second kernel
- * recomputes the marked ones (zero columns, subnormal entries, entries
- * spanning the exponent range) with the general sequences -- the same
- * correctly rounded results either way.  Each call takes a 256-byte flag block
- * from a stream-ordered memory pool that the library creates per device on
- * first use (it keeps what it allocates until the process exits). */
+ * Two kernels and a flag block per call, as svd2_batch_d. */
 int svd2_batch_s(int64_t n, const float *const A[4], float *const U[4],
                  float *const V[4], float *smax, float *smin, int32_t *s,
                  uint32_t flags, svd2_stream_t stream);

@@ -340,28 +340,24 @@ inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *con
     grid = grid_for(units, L, resident);
     block = (unsigned)L.block;
   }
-  if constexpr (!kHotFlags<T>) {
-    k<<<(unsigned)grid, block, 0, stream>>>(p);
-    SVD2_CUDA_TRY(cudaGetLastError());
-    return SVD2_OK;
-  } else {
-    void *flag = nullptr;
-    int rc = flag_block(stream, &flag);
-    if (rc != SVD2_OK) return rc;
-    p.redo = static_cast<unsigned long long *>(flag);
-    k<<<(unsigned)grid, block, 0, stream>>>(p);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) {
-      if (vals)
-        fix_kernel<T, CPLX, true><<<fix_grid(n), 256, 0, stream>>>(p);
-      else
-        fix_kernel<T, CPLX, false><<<fix_grid(n), 256, 0, stream>>>(p);
-      e = cudaGetLastError();
-    }
-    rc = flag_release(flag, stream);
-    if (e != cudaSuccess) return record_cuda_error(e);
-    return rc;
+  // the batch kernel, then the fix-up pass, which reads the flag word and
+  // ends unless the batch kernel flagged a matrix
+  void *flag = nullptr;
+  int rc = flag_block(stream, &flag);
+  if (rc != SVD2_OK) return rc;
+  p.redo = static_cast<unsigned long long *>(flag);
+  k<<<(unsigned)grid, block, 0, stream>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    if (vals)
+      fix_kernel<T, CPLX, true><<<fix_grid(n), 256, 0, stream>>>(p);
+    else
+      fix_kernel<T, CPLX, false><<<fix_grid(n), 256, 0, stream>>>(p);
+    e = cudaGetLastError();
   }
+  rc = flag_release(flag, stream);
+  if (e != cudaSuccess) return record_cuda_error(e);
+  return rc;
 }
 
 // The interleaved layout of a (n, 2, 2) row-major array (torch's layout for a

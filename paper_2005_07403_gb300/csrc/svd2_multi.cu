@@ -309,17 +309,14 @@ static int multi_launch(const void *plan, int block, int mpt, int unroll, int gr
   if (rc == SVD2_OK) rc = multi_grid(kz, block, grid, tz, &gz);
   if (rc != SVD2_OK) return rc;
   const auto *pl = static_cast<const unsigned char *>(plan);
-  if (kHotFlags<double>)
-    SVD2_CUDA_TRY(cudaMemsetAsync(const_cast<unsigned char *>(pl) + kRedoOffset, 0,
-                                  sizeof(unsigned long long), st));
+  SVD2_CUDA_TRY(cudaMemsetAsync(const_cast<unsigned char *>(pl) + kRedoOffset, 0,
+                                sizeof(unsigned long long), st));
   kr<<<gr, block, 0, st>>>(pl);
   SVD2_CUDA_TRY(cudaGetLastError());
   kz<<<gz, block, 0, st>>>(pl);
   SVD2_CUDA_TRY(cudaGetLastError());
-  if (kHotFlags<double>) {
-    multi_fix_kernel<<<sm_count() * 4, 256, 0, st>>>(pl);
-    SVD2_CUDA_TRY(cudaGetLastError());
-  }
+  multi_fix_kernel<<<sm_count() * 4, 256, 0, st>>>(pl);
+  SVD2_CUDA_TRY(cudaGetLastError());
   return SVD2_OK;
 }
 

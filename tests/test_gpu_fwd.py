@@ -171,7 +171,7 @@ def test_zero_length_is_noop():
 def sprinkled(n, rows, dtype, seed, every=997):
     """N(0,1) batch with an edge matrix (zeros, subnormals, the top of the
     exponent range, pivot ties) at every `every`-th position from 3: the
-    matrices the fast single-precision arithmetic hands to the fix-up pass,
+    matrices the fast arithmetic of the batch kernels hands to the fix-up pass,
     scattered over blocks, vector lanes and the ragged tail."""
     A = inputs.normal_batch(n, rows, seed, dtype)
     E = inputs.edge_real(dtype)
@@ -186,14 +186,15 @@ def sprinkled(n, rows, dtype, seed, every=997):
     return np.ascontiguousarray(A)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("rows", [4, 8])
 @pytest.mark.parametrize("backscale", [False, True])
-def test_fp32_fixup_pass_scattered_edges(rows, backscale):
-    """The FP32 kernels finish ordinary matrices on branch-free fast forms and
+def test_fixup_pass_scattered_edges(dtype, rows, backscale):
+    """The batch kernels finish ordinary matrices on branch-free fast forms and
     leave the rest (s = INT32_MIN) to a second pass with the general
     arithmetic: the combined result must equal the oracle bit for bit, and no
     sentinel may remain."""
-    A = sprinkled(2**18 + 5, rows, np.float32, 71 + rows)
+    A = sprinkled(2**18 + 5, rows, dtype, 71 + rows)
     g = gpu_svd2(A, backscale=backscale)
     with np.errstate(all="ignore"):
         o = oracle.svd2(A, backscale=backscale)

@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_2005_07403_gb300 import inputs
 from paper_2005_07403_gb300 import svd2 as S
-from tests.test_gpu_fwd import assert_same
+from tests.test_gpu_fwd import assert_same, sprinkled
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +24,8 @@ def _batches(count, seed, lo=0, hi=3000):
         A = inputs.normal_batch(int(n), rows, seed * 1000 + i)
         if i % 7 == 3 and not c and n > 0:
             A = inputs.real_mixed(int(n), seed=seed * 1000 + i)
+        if i % 7 == 5 and c and n > 0:      # complex edge matrices for the fix-up pass
+            A = sprinkled(int(n), 8, np.float64, seed * 1000 + i, every=13)
         out.append(A)
     return out
 
