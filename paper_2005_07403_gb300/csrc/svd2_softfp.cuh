@@ -204,13 +204,12 @@ SFP_FN double div_core(uint64_t ua, uint64_t ub, uint64_t sgn, int e0) {
   const int32_t q2 = f2i_small(fmul(fmul(i2f_small((int32_t)(R >> 34)), r), 65536.0f));
   R = (int64_t)(((uint64_t)R << 11) - mulw(q2, mb));                    // |R| < 0.51 mb
   uint64_t Q = ((uint64_t)q0 << 29) + ((uint64_t)(int64_t)q1 << 11) + (uint64_t)(int64_t)q2;
-  // exact floor and remainder: R = A 2^52 - Q mb in [0, mb)
-  if (R < 0) { Q -= 1; R += (int64_t)mb; }
-  if (R < 0) { Q -= 1; R += (int64_t)mb; }
-  if (R >= (int64_t)mb) { Q += 1; R -= (int64_t)mb; }
-  // round to nearest, ties to even
-  const uint64_t twoR = (uint64_t)R << 1;
-  Q += (twoR > mb || (twoR == mb && (Q & 1))) ? 1 : 0;
+  // R = A 2^52 - Q mb exactly, |R| < 0.51 mb: the exact quotient A 2^52 / mb
+  // is within 0.51 of Q, so its nearest integer is Q + 1 when 2R > mb, Q - 1
+  // when 2R < -mb and Q otherwise.  No tie arises: the quotient of two binary
+  // floating-point numbers is never half way between two representable ones.
+  const int64_t twoR = R * 2, m = (int64_t)mb;                           // |2R| < 2^54.1
+  Q = Q + (twoR > m ? 1 : 0) - (twoR < -m ? 1 : 0);
   // Q in [2^52, 2^53]; Q = 2^53 carries into the exponent field
   return dval(sgn | (((uint64_t)(e - 1) << 52) + Q));
 }
@@ -272,12 +271,12 @@ SFP_FN double sqrt_core(uint64_t ux) {
   // R = X 2^52 - S^2 = R2 2^22 - 2 S2 d2 - d2^2, |R| < 2^55
   int64_t R = (int64_t)(((uint64_t)R2 << 22) - (mulw(d2, S2) << 1) -
                         (uint64_t)((int64_t)d2 * d2));
-  // exact floor: R = X 2^52 - S^2 in [0, 2S]
-  if (R < 0) { R += (int64_t)(2 * S - 1); S -= 1; }
-  if (R < 0) { R += (int64_t)(2 * S - 1); S -= 1; }
-  if (R > (int64_t)(2 * S)) { R -= (int64_t)(2 * S + 1); S += 1; }
-  // round to nearest (a square root is never half way): up iff R > S
-  S += (R > (int64_t)S) ? 1 : 0;
+  // the exact root t = sqrt(X 2^52) is within 0.53 of S, so its nearest
+  // integer (t is never half way) is S + 1 when t > S + 1/2, i.e. R > S + 1/4,
+  // i.e. R > S; S - 1 when t < S - 1/2, i.e. R < 1/4 - S, i.e. R <= -S; and
+  // S otherwise (R integer)
+  const int64_t si = (int64_t)S;
+  S = S + (R > si ? 1 : 0) - (R <= -si ? 1 : 0);
   return dval(((uint64_t)(er - 1) << 52) + S);
 }
 
