@@ -116,10 +116,15 @@ def sm_max_mhz():
 # x 2.07 GHz).  Their roofline counts the method's FP64 add, mul and fma per
 # matrix (divisions and square roots run on the integer and FP32 pipes and are
 # not counted); sign, exponent, min/max and pivot steps are bit operations.
+# Counted from the formulas: complex 3 add + 36 fma + 50 mul (8 hypot, Eq. 4,
+# Eq. 6 - Eq. 9, Fig. 10, the expansion of Eq. 29); real 3 add + 14 fma + 17
+# mul.  The ncu opcode counts of the kernels agree exactly.
 GB300_SMS = 152
 GB300_FP64_PER_SM_CLK = 2
 GB300_SM_MAX_MHZ = 2070.0
-FP64_OPS_PER_MATRIX = {"z": 91, "d": 34}
+FP64_OPS_PER_MATRIX = {"z": 89, "d": 34}
+# the values-only complex method skips Eq. 29 (U: 12 fma + 21 mul; V: 5 mul)
+FP64_OPS_VALUES_Z = 89 - 38
 
 
 # The translation unit each workload's kernels are built from; every digest
@@ -313,9 +318,10 @@ def time_steps(torch, call, steps, warmup, stream):
 
 
 def _quantile(torch, x, q):
-    """The q-quantile of a 1-D tensor (k-th smallest, k = ceil(q * numel))."""
+    """The q-quantile of a tensor (the k-th smallest, k = ceil(q * numel)), by a
+    device sort (torch.kthvalue takes ~0.7 s on 2^26 elements)."""
     k = max(1, int(np.ceil(q * x.numel())))
-    return float(torch.kthvalue(x.flatten().cpu() if x.numel() > 2**27 else x.flatten(), k).values)
+    return float(torch.sort(x.flatten()).values[k - 1])
 
 
 def error_metrics(torch, A, r):
@@ -532,9 +538,9 @@ def bench_variants(torch, S, stream, steps=10, warmup=3):
                  "hbm_frac": bpm * n / (ms / 1e3) / 1e9 / peak}
             res[form] = r
         if rows == 8:
-            # the values-only complex method skips Eq. 29: 53 of its 91 FP64 operations remain
-            res["values_only"]["fp64_pipe_frac"] = 53 * n / (res["values_only"]["ms"] / 1e3) / 1e9 / fp64_peak
-            res["interleaved"]["fp64_pipe_frac"] = 91 * n / (res["interleaved"]["ms"] / 1e3) / 1e9 / fp64_peak
+            zv, zf = FP64_OPS_VALUES_Z, FP64_OPS_PER_MATRIX["z"]
+            res["values_only"]["fp64_pipe_frac"] = zv * n / (res["values_only"]["ms"] / 1e3) / 1e9 / fp64_peak
+            res["interleaved"]["fp64_pipe_frac"] = zf * n / (res["interleaved"]["ms"] / 1e3) / 1e9 / fp64_peak
         out[name] = dict(n=n, **res)
         del A, M, vals
         torch.cuda.empty_cache()
