@@ -53,6 +53,9 @@ WORKLOADS = {
     "real-fp32-rerun": dict(rows=4, n=2**26, bytes_per=16 + 32 + 8 + 4, kind="s", form="rerun",
                             dtype="f32",
                             desc="real FP32 n=2^26 with FP64 re-run below tau = 2^-8"),
+    "complex64": dict(rows=8, n=2**25, bytes_per=32 + 64 + 8 + 4, kind="c", form="plain",
+                      dtype="f32",
+                      desc="complex FP32 n=2^25 (90% N(0,1), 10% ill-conditioned), no re-run"),
     "complex64-rerun": dict(rows=8, n=2**25, bytes_per=32 + 64 + 8 + 4, kind="c", form="rerun",
                             dtype="f32",
                             desc="complex FP32 n=2^25 (90% N(0,1), 10% ill-conditioned) with "
@@ -64,7 +67,7 @@ def make_input(name, n, rank):
     from paper_2005_07403_gb300 import inputs
     if name == "complex128":
         return inputs.complex_scaled(n, seed=inputs.SEED_CFG2 + rank)
-    if name == "complex64-rerun":
+    if name in ("complex64", "complex64-rerun"):
         return inputs.complex_fp32_illcond(n, seed=inputs.SEED_CFG3 + 100 + rank)[0]
     A32, _ = inputs.real_fp32_illcond(n, seed=inputs.SEED_CFG3 + rank)
     return A32.astype(np.float64) if name == "real-fp64" else A32
@@ -131,7 +134,7 @@ FP64_OPS_VALUES_Z = 89 - 38
 # also covers the shared headers, the C header and the build script.
 KERNEL_SOURCES = {"complex128": "svd2_fwd_z.cu", "real-fp64": "svd2_fwd_d.cu",
                   "real-fp32": "svd2_fwd_s.cu", "real-fp32-rerun": "svd2_rerun.cu",
-                  "complex64-rerun": "svd2_rerun.cu"}
+                  "complex64": "svd2_fwd_c.cu", "complex64-rerun": "svd2_rerun.cu"}
 
 
 def sources_digest(workload):
