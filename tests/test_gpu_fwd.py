@@ -106,6 +106,9 @@ def test_fp32_real_and_complex():
     check(A32, "s illcond")
     check(inputs.normal_batch(2**15 + 1, 8, 23, np.float32), "c normal")
     check(inputs.random_bits_f32(2**15, 8, 24), "c rbits")
+    Z32, _ = inputs.complex_fp32_illcond(2**15 + 7, seed=25)
+    check(Z32, "c illcond")
+    check(Z32.astype(np.float64), "z illcond widened")
 
 
 # ----------------------------------------------------------- options/shapes
