@@ -184,9 +184,9 @@ SFP_FN uint64_t mulw(int64_t a, uint64_t b) { return (uint64_t)a * b; }
 // digits, sign and exponent attached.
 SFP_FN double div_core(uint64_t ua, uint64_t ub, uint64_t sgn, int e0) {
   const uint64_t ma = (ua & kFrac) | kImpl, mb = (ub & kFrac) | kImpl;
-  const bool lt = ma < mb;
-  const uint64_t A = lt ? ma << 1 : ma;     // A in [mb, 2 mb): A/mb in [1, 2)
-  const int e = e0 - (lt ? 1 : 0);
+  const int lt = ma < mb ? 1 : 0;
+  const uint64_t A = ma << lt;              // A in [mb, 2 mb): A/mb in [1, 2)
+  const int e = e0 - lt;
   // Q = floor(A 2^52 / mb) in [2^52, 2^53), built as q0 2^29 + q1 2^11 + q2.
   const float fb = fval(0x4B000000u | ((uint32_t)(mb >> 29) & 0x7FFFFFu));   // mb >> 29, exact
   const float fa = fval(0x4B000000u | ((uint32_t)(ma >> 29) & 0x7FFFFFu));   // ma >> 29, exact
@@ -203,15 +203,17 @@ SFP_FN double div_core(uint64_t ua, uint64_t ub, uint64_t sgn, int e0) {
   // digit 2 (11 bits): q2 ~ R 2^11 / mb ~ (R >> 34) r 2^16, |q2| < 2^13; error < 0.51
   const int32_t q2 = f2i_small(fmul(fmul(i2f_small((int32_t)(R >> 34)), r), 65536.0f));
   R = (int64_t)(((uint64_t)R << 11) - mulw(q2, mb));                    // |R| < 0.51 mb
-  uint64_t Q = ((uint64_t)q0 << 29) + ((uint64_t)(int64_t)q1 << 11) + (uint64_t)(int64_t)q2;
-  // R = A 2^52 - Q mb exactly, |R| < 0.51 mb: the exact quotient A 2^52 / mb
-  // is within 0.51 of Q, so its nearest integer is Q + 1 when 2R > mb, Q - 1
-  // when 2R < -mb and Q otherwise.  No tie arises: the quotient of two binary
-  // floating-point numbers is never half way between two representable ones.
+  // R = A 2^52 - Q mb exactly for Q = q0 2^29 + q1 2^11 + q2, |R| < 0.51 mb:
+  // the exact quotient A 2^52 / mb is within 0.51 of Q, so its nearest integer
+  // is Q + 1 when 2R > mb, Q - 1 when 2R < -mb and Q otherwise.  No tie
+  // arises: the quotient of two binary floating-point numbers is never half
+  // way between two representable ones.
   const int64_t twoR = R * 2, m = (int64_t)mb;                           // |2R| < 2^54.1
-  Q = Q + (twoR > m ? 1 : 0) - (twoR < -m ? 1 : 0);
-  // Q in [2^52, 2^53]; Q = 2^53 carries into the exponent field
-  return dval(sgn | (((uint64_t)(e - 1) << 52) + Q));
+  const int32_t q2r = q2 + (twoR > m ? 1 : 0) - (twoR < -m ? 1 : 0);
+  // the result's significand (in [2^52, 2^53]; 2^53 carries into the exponent
+  // field) added to the exponent field of e - 1
+  return dval(sgn | ((((uint64_t)(e - 1) << 52) + ((uint64_t)q0 << 29)) +
+                     ((uint64_t)(int64_t)q1 << 11) + (uint64_t)(int64_t)q2r));
 }
 
 // RN(a / b) on the fast domain -- b normal, and a = +-0 or a normal with the
