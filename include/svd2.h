@@ -289,9 +289,10 @@ int svd2_bwd_c(int64_t n, const float *const U[8], const float *const V[8],
  *   of 32 in 32..512, mpt in {1, 2}, unroll in {1, 2}) to the caller-owned
  *   device buffer `plan` (16-byte aligned) with a synchronous copy, and returns
  *   the tile count in *total_tiles (may be NULL).  descs is a host array.
- * svd2_multi_run: one launch per kind over the plan, asynchronous on
- *   `stream`; block, mpt and unroll must be those of the plan (otherwise the
- *   launch does nothing).  grid 0: one block per tile for a plan prepared in
+ * svd2_multi_run: one launch per kind over the plan, then the fix-up pass
+ *   over every batch (reads the plan's flag word and ends when nothing was
+ *   marked), asynchronous on `stream`; block, mpt and unroll must be those of
+ *   the plan (otherwise the launch does nothing).  grid 0: one block per tile for a plan prepared in
  *   this process (the tile counts are remembered on the host; the fastest on
  *   GB300), else SMs x resident blocks; grid > 0: that many blocks, a
  *   persistent grid walking the tiles when it is at most the resident count.

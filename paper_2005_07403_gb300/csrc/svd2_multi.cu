@@ -14,7 +14,9 @@
 // graph and replayed every step.  Real and complex batches form
 // two tile sequences, each walked by its own persistent kernel (launched one
 // after the other), so each kernel carries only its own variant of the method
-// and keeps its own register budget.
+// and keeps its own register budget.  A third kernel, the fix-up pass,
+// recomputes with the general arithmetic the matrices the fast arithmetic
+// marked (it reads the plan's flag word and ends when there are none).
 #include <cstddef>
 #include <mutex>
 #include <new>
