@@ -269,17 +269,16 @@ SFP_FN double sqrt_core(uint64_t ux) {
                                (uint64_t)((int64_t)d1 * d1));
   // digit 2 (11 bits): d2 ~ R2 2^22 / (2 S2) ~ (R2 >> 24) y 2^4, |d2| < 2^13.6; error < 0.53
   const int32_t d2 = f2i_small(fmul(fmul(i2f_small((int32_t)(R2 >> 24)), y), 16.0f));
-  uint64_t S = S2 + (uint64_t)(int64_t)d2;
+  const int64_t si = (int64_t)(S2 + (uint64_t)(int64_t)d2);                 // S
   // R = X 2^52 - S^2 = R2 2^22 - 2 S2 d2 - d2^2, |R| < 2^55
-  int64_t R = (int64_t)(((uint64_t)R2 << 22) - (mulw(d2, S2) << 1) -
-                        (uint64_t)((int64_t)d2 * d2));
+  const int64_t R = (int64_t)(((uint64_t)R2 << 22) - (mulw(d2, S2) << 1) -
+                              (uint64_t)((int64_t)d2 * d2));
   // the exact root t = sqrt(X 2^52) is within 0.53 of S, so its nearest
   // integer (t is never half way) is S + 1 when t > S + 1/2, i.e. R > S + 1/4,
   // i.e. R > S; S - 1 when t < S - 1/2, i.e. R < 1/4 - S, i.e. R <= -S; and
-  // S otherwise (R integer)
-  const int64_t si = (int64_t)S;
-  S = S + (R > si ? 1 : 0) - (R <= -si ? 1 : 0);
-  return dval(((uint64_t)(er - 1) << 52) + S);
+  // S otherwise (R integer); the adjustment joins the last digit
+  const int32_t d2r = d2 + (R > si ? 1 : 0) - (R <= -si ? 1 : 0);
+  return dval((((uint64_t)(er - 1) << 52) + S2) + (uint64_t)(int64_t)d2r);
 }
 
 // RN(sqrt(x)) for positive normal x, without a branch; for any other x (+-0,
