@@ -1,6 +1,7 @@
 // Host check of the integer-pipe IEEE division and square root
-// (paper_2005_07403_gb300/csrc/svd2_softfp.cuh) against the CPU's correctly
-// rounded hardware division and square root, bit for bit.  The header's host
+// (paper_2005_07403_gb300/csrc/svd2_softfp.cuh), in their general and
+// branch-free forms (the latter where they do not flag the operands), against
+// the CPU's correctly rounded hardware division and square root, bit for bit.  The header's host
 // build replaces the FP32 approximate reciprocals by the nearest float moved
 // by up to +-2 units in the last place, wider than the GPU instructions'
 // error.  Usage: softfp_host_check <count per class> <seed>; prints the
@@ -26,6 +27,25 @@ static uint64_t sm64(uint64_t &s) {  // SplitMix64
 
 static long long checked = 0, bad = 0;
 
+// the branch-free forms: where they do not flag the operands, the same bits
+static void chk_div_fast(double a, double b, double h) {
+  unsigned flag = 0;
+  const double r = svd2::sfp::div_fast(a, b, flag);
+  ++checked;
+  if (!flag && dbits(r) != dbits(h)) {
+    if (bad < 10) std::printf("div_fast mismatch a=%a b=%a soft=%a hw=%a\n", a, b, r, h);
+    ++bad;
+  }
+}
+static void chk_sqrt_fast(double x, double h) {
+  unsigned flag = 0;
+  const double r = svd2::sfp::sqrt_fast(x, flag);
+  ++checked;
+  if (!flag && dbits(r) != dbits(h)) {
+    if (bad < 10) std::printf("sqrt_fast mismatch x=%a soft=%a hw=%a\n", x, r, h);
+    ++bad;
+  }
+}
 static void chk_div(double a, double b) {
   const double r = svd2::sfp::div_rn(a, b), h = a / b;
   ++checked;
@@ -33,6 +53,7 @@ static void chk_div(double a, double b) {
     if (bad < 10) std::printf("div mismatch a=%a b=%a soft=%a hw=%a\n", a, b, r, h);
     ++bad;
   }
+  chk_div_fast(a, b, h);
 }
 static void chk_sqrt(double x) {
   const double r = svd2::sfp::sqrt_rn(x), h = std::sqrt(x);
@@ -41,6 +62,7 @@ static void chk_sqrt(double x) {
     if (bad < 10) std::printf("sqrt mismatch x=%a soft=%a hw=%a\n", x, r, h);
     ++bad;
   }
+  chk_sqrt_fast(x, h);
 }
 
 static void chk_d2f(double x) {
@@ -88,6 +110,10 @@ int main(int argc, char **argv) {
                        0x7f800001u, 0x3f800000u})
       chk_f2d(b | (sg ? 0x80000000u : 0u));
   }
+  // zero numerators over normal divisors, both signs: the fast form's signed zero
+  for (int sa = 0; sa < 2; ++sa)
+    for (int sb = 0; sb < 2; ++sb)
+      for (uint64_t e : {1ull, 1023ull, 2046ull}) chk_div(mk(sa, 0, 0), mk(sb, e, 0x123456789abcull));
   for (long long i = 0; i < n; ++i) {
     // conversions: any float pattern; doubles around the float range (float
     // subnormal results, overflow), with the 29 dropped bits random, exactly
