@@ -264,3 +264,15 @@ def test_full_size_complex_workload_sampled():
 def test_full_size_fp32_workload_sampled():
     A32, _ = inputs.real_fp32_illcond(2**26)
     _sampled_check(A32, "fp32 2^26")
+
+
+def test_full_size_fp64_workload_sampled():
+    """The FP32-vs-FP64 batch at n = 2^26 through the FP64 form (the exact
+    widening of the FP32 values), on 2^15 sampled matrices."""
+    A32, _ = inputs.real_fp32_illcond(2**26)
+    _sampled_check(A32.astype(np.float64), "fp64 2^26")
+
+
+def test_full_size_complex64_workload_sampled():
+    Z32, _ = inputs.complex_fp32_illcond(2**25)
+    _sampled_check(Z32, "complex64 2^25")
