@@ -148,11 +148,6 @@ SFP_FN float rsqrt_approx(float x) {
 SFP_FN float i2f_small(int32_t x) { return fadd(fval(0x4B400000u + (uint32_t)x), -12582912.0f); }
 // the nearest integer to y, for |y| < 2^22.
 SFP_FN int32_t f2i_small(float y) { return (int32_t)(fbits(fadd(y, 12582912.0f)) - 0x4B400000u); }
-// an integer v in [2^22, 2^24) as a float, exactly.
-SFP_FN float u24_to_f(uint32_t v) {
-  return v >= 0x800000u ? fval(0x4B000000u | (v & 0x7FFFFFu))
-                        : fval(0x4A800000u | ((v << 1) & 0x7FFFFFu));
-}
 // the integer nearest to a float y in about [2^23 - 8, 2^24 + 8], clamped to [2^23, 2^24 - 1].
 SFP_FN uint32_t f_to_u24_clamped(float y) {
   const float c = y < 8388608.0f ? 8388608.0f : (y > 16777215.0f ? 16777215.0f : y);
@@ -253,12 +248,15 @@ SFP_FN double sqrt_core(uint64_t ux) {
   const uint64_t X = mx << odd;                    // X in [2^52, 2^54), E - odd even
   const int er = ((E - odd) >> 1) + 1023;          // result exponent, always normal
   // S = floor(sqrt(X 2^52)) in [2^52, 2^53), built as s0 2^29 + d1 2^11 + d2.
-  const float fx = u24_to_f((uint32_t)(X >> 30));  // X >> 30 in [2^22, 2^24), exact
+  // fx = X / 2^30 to 24 bits: the top 24 bits of mx as a float in [2^23, 2^24),
+  // halved (exponent field minus one) when X = mx, i.e. E even
+  const float fx = fval((0x4B000000u | ((uint32_t)(mx >> 29) & 0x7FFFFFu)) - ((uint32_t)(odd ^ 1) << 23));
   const float y = rsqrt_approx(fx);                // ~fx^-1/2
   // digit 0 (24 bits): s0 ~ sqrt(fx) 2^12 ~ S / 2^29, within 8.5
   const uint32_t s0 = f_to_u24_clamped(fmul(fmul(fx, y), 4096.0f));
-  // R1 = (X 2^52 - (s0 2^29)^2) / 2^52 exactly; |R1| < 2^34.1
-  const int64_t R1 = (int64_t)(X - (((uint64_t)s0 * s0) << 6));
+  // R1 = (X 2^52 - (s0 2^29)^2) / 2^52 = X - (8 s0)^2 exactly (8 s0 < 2^27); |R1| < 2^34.1
+  const uint32_t s08 = s0 << 3;
+  const int64_t R1 = (int64_t)(X - (uint64_t)s08 * s08);
   // digit 1 (18 bits): the Newton step S - s0 2^29 ~ R1 2^52 / (2 s0 2^29), in units of
   // 2^11: d1 ~ R1 / (2 s0) 2^12 ~ R1 y / 2 (1/s0 ~ y 2^-12); |d1| < 2^21.1;
   // error <= 2 (truncation) + 2.3 (y for 1/s0) + 1.1 (Newton's square term) + 0.5
