@@ -394,6 +394,22 @@ int svd2_get_launch(int op, int *block, int *mpt, int *unroll, int *waves);
 int svd2_arith_check(int op, int64_t n, const double *x, const double *y, double *lib,
                      double *hw, svd2_stream_t stream);
 
+/*
+ * Self-test of the single-precision branch-free reciprocal, square root and
+ * division (Markstein's method) against the hardware's correctly rounded
+ * sequences (__frcp_rn, __fsqrt_rn, __fdiv_rn), on indices k in
+ * [begin, begin + count): op 0: the reciprocal of the float with bit pattern
+ * k; op 1: the square root of the float with bit pattern k; op 2: a / b for a,
+ * b in [1, 2) with significands k >> 23 and k & 0x7fffff (k < 2^46); op 3: a /
+ * b for the two floats of a counter-based random 64-bit pattern of k, counted
+ * only where b is in [2^-125, 2^125] and a is zero or |a| >= 2^-102 with
+ * |a / b| in [2^-125, 2^127].  result: device memory of 3 uint64, which the caller initialises to
+ * {0, UINT64_MAX, 0}: [0] gains the mismatches, [1] becomes the smallest
+ * mismatching k, [2] gains the cases checked.  Asynchronous on `stream`.
+ */
+int svd2_fp32_selfcheck(int op, uint64_t begin, uint64_t count, void *result,
+                        svd2_stream_t stream);
+
 /* The cudaError_t of the last failed CUDA call made by this thread (0 if none). */
 int svd2_last_cuda_error(void);
 

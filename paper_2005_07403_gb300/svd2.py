@@ -143,6 +143,8 @@ def _declare(L):
     L.svd2_batch_host.restype = ctypes.c_int
     L.svd2_arith_check.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, P, P]
     L.svd2_arith_check.restype = ctypes.c_int
+    L.svd2_fp32_selfcheck.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, P, P]
+    L.svd2_fp32_selfcheck.restype = ctypes.c_int
     L.svd2_set_launch.argtypes = [ctypes.c_int] * 5
     L.svd2_set_launch.restype = ctypes.c_int
     L.svd2_get_launch.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4
@@ -410,6 +412,21 @@ def arith_check(op: str, x: torch.Tensor, y: torch.Tensor | None = None):
                                 hw_out.data_ptr(), current_stream_handle(x.device))
     check(rc, "svd2_arith_check")
     return lib_out, hw_out
+
+
+def fp32_selfcheck(op: str, begin: int, count: int, device="cuda") -> dict:
+    """The branch-free single-precision "rcp", "sqrt", "div_sig" (significand
+    pairs) or "div_rand" (random operands on the stated domain) against the
+    hardware's correctly rounded sequences over indices [begin, begin + count)
+    (svd2_fp32_selfcheck); returns mismatches, first mismatching index, cases
+    checked."""
+    res = torch.tensor([0, -1, 0], dtype=torch.int64, device=device)   # -1: UINT64_MAX
+    code = {"rcp": 0, "sqrt": 1, "div_sig": 2, "div_rand": 3}[op]
+    rc = lib().svd2_fp32_selfcheck(code, int(begin), int(count), res.data_ptr(),
+                                   current_stream_handle(res.device))
+    check(rc, "svd2_fp32_selfcheck")
+    v = res.cpu().tolist()
+    return {"mismatches": v[0], "first": v[1] & (2**64 - 1), "checked": v[2]}
 
 
 def default_rel_delta(dtype) -> float:

@@ -92,3 +92,37 @@ def test_widening_from_float_matches_hardware():
     lib, hw = S.arith_check("f2d", x)
     torch.cuda.synchronize()
     assert _same(lib, hw)
+
+
+# ------------------------------------------- single precision, branch-free forms
+
+def _selfcheck(op, begin, count):
+    r = S.fp32_selfcheck(op, begin, count)
+    assert r["mismatches"] == 0, (op, hex(r["first"]), r)
+    return r
+
+
+def test_fp32_reciprocal_exhaustive():
+    """The branch-free reciprocal equals __frcp_rn on every float in
+    [2^-125, 2^125] (its stated range)."""
+    lo, hi = 0x01000000, 0x7C000000          # 2^-125 .. 2^125
+    r = _selfcheck("rcp", lo, hi - lo + 1)
+    assert r["checked"] == hi - lo + 1
+
+
+def test_fp32_sqrt_exhaustive():
+    """The branch-free square root equals __fsqrt_rn on every float in
+    [1, FLT_MAX] (its stated range)."""
+    lo, hi = 0x3F800000, 0x7F7FFFFF
+    _selfcheck("sqrt", lo, hi - lo + 1)
+
+
+def test_fp32_division_significand_pairs():
+    """The branch-free division equals __fdiv_rn on 2^36 significand pairs (8
+    runs of 1024 consecutive significands of a spread over [1, 2), each against
+    every b in [1, 2)), and on 2^32 random operand pairs inside its stated
+    domain."""
+    for c in range(8):
+        _selfcheck("div_sig", c << 43, 1 << 33)
+    r = _selfcheck("div_rand", 0, 1 << 32)
+    assert r["checked"] > 1 << 28
