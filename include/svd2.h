@@ -182,7 +182,11 @@ int svd2_kog_skipped(const void *workspace, int64_t *count);
  * u * sigma'_max / sigma'_min relative error from r''_22, Fig. 8); a kept
  * matrix has sigma'_min / sigma'_max >= 2^tau_log2, bounding that error.
  * tau_log2 in [-100, 0]; the library's measured default is SVD2_RERUN_TAU_LOG2.
- * workspace: device memory of at least svd2_rerun_workspace_bytes(n) bytes,
+ * Four kernels on the stream: the single-precision batch kernel, which marks
+ * the matrices to re-run; a compaction of their indices into the workspace;
+ * the double-precision re-run of the listed matrices; the fix-up pass.
+ * workspace: device memory of at least svd2_rerun_workspace_bytes(n) bytes
+ * (256 bytes plus 4 per matrix for the index list),
  * 16-byte aligned, caller-owned, used by this call only (two calls sharing a
  * workspace must be ordered on one stream).  After the call completes, its
  * first 8 bytes hold the number of re-run matrices (uint64), see

@@ -1,10 +1,10 @@
 // svd2_batch_s_rerun_noalloc: the FP32 form with FP64 re-run for callers that
 // cannot allocate device memory.
 //
-// The re-run form needs scratch memory: the call's re-run count and the flag
-// of its fix-up pass, in a workspace whose size formula also reserves room for
-// an index list (unused: the queue of matrices to re-run lives in shared
-// memory).  svd2_batch_s_rerun takes that scratch from the caller.  Some callers cannot provide it: an application whose device memory
+// The re-run form needs scratch memory: the call's re-run count, the flag of
+// its fix-up pass and the index list of the matrices to re-run (4 bytes per
+// matrix).  svd2_batch_s_rerun takes that scratch from the caller.  Some
+// callers cannot provide it: an application whose device memory
 // is entirely owned by another allocator (a framework's caching pool, or a host
 // program that hands this library only the input and output buffers), or code
 // that must not call cudaMalloc once it is running (cudaMalloc may synchronise
@@ -18,8 +18,8 @@
 // array's device address with cudaGetSymbolAddress (no allocation) and caches
 // it; make that first call before any stream capture.  In host code the array's
 // name is only a host-side stand-in, so the kernels always receive the looked-up
-// address.  All calls on a device share the one array: the count and the flag
-// are cleared at the start of each call, and calls whose
+// address.  All calls on a device share the one array: the count, the flag and
+// the list length are cleared at the start of each call, and calls whose
 // work can overlap on the GPU -- on different streams without ordering between
 // them -- race on it and must not be made.
 #include <mutex>
