@@ -178,10 +178,11 @@ inline unsigned fix_grid(int64_t n) {
 }
 
 // Minimum resident 512-thread blocks per SM the compiler must allow for: the
-// FP64 kernels are bound by arithmetic latency and run best at 64 registers
-// (32 warps per SM); the FP32 ones may use up to 128 (capping them at 32
+// FP64 kernels and the complex FP32 one are bound by arithmetic latency and
+// run best at 64 registers (32 warps per SM; complex FP32 at 76 registers
+// measured 5% slower); the real FP32 one may use up to 128 (capping it at 32
 // registers for full occupancy measured no faster).
-template <typename T, bool CPLX> constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 1;
+template <typename T, bool CPLX> constexpr int kMinBlocks = (sizeof(T) == 8 || CPLX) ? 2 : 1;
 
 template <typename T, bool CPLX, int M, int UNR, bool VALS = false, bool MARK = false>
 __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
