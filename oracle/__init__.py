@@ -88,7 +88,7 @@ def _declare(lib):
         f = getattr(lib, name)
         f.argtypes = [_I64, pp, pp, pp, _P, _P, _P, _P, ctypes.c_uint32, ctypes.c_int]
         f.restype = None
-    for name in ("svd2o_batch_s_rerun", "svd2o_batch_c_rerun"):
+    for name in ("svd2o_batch_s_rerun", "svd2o_batch_c_rerun", "svd2o_batch_s_tan64"):
         f = getattr(lib, name)
         f.argtypes = [_I64, pp, pp, pp, _P, _P, _P, _P, ctypes.c_int, ctypes.c_uint32,
                       ctypes.c_int]
@@ -199,6 +199,27 @@ class Oracle:
         cnt = f(n, _ptrs(A), _ptrs(U), _ptrs(V), _p(smax), _p(smin), _p(s), _p(flagged),
                 int(tau_log2), BACKSCALE if backscale else 0, nthreads)
         return dict(U=U, V=V, smax=smax, smin=smin, s=s, flagged=flagged, count=int(cnt))
+
+
+    def svd2_tan64(self, A, tau_log2: int, *, backscale: bool = False, nthreads: int = 0):
+        """FP32 form with the FP64 tangent step for the matrices with
+        |r''_22| < 2^tau_log2 r11 (Eq. 6 - Eq. 7 in double, the rest in float).
+
+        ``A`` is float32 of shape (4, n).  Returns the dict of ``svd2`` plus
+        ``wide`` (uint8, 1 where the step ran in double) and ``count``.
+        """
+        A = _as(np.asarray(A), np.float32, 4)
+        n = A.shape[1]
+        U = np.empty_like(A)
+        V = np.empty_like(A)
+        smax = np.empty(n, np.float32)
+        smin = np.empty(n, np.float32)
+        s = np.empty(n, np.int32)
+        wide = np.empty(n, np.uint8)
+        cnt = self.lib.svd2o_batch_s_tan64(n, _ptrs(A), _ptrs(U), _ptrs(V), _p(smax), _p(smin),
+                                           _p(s), _p(wide), int(tau_log2),
+                                           BACKSCALE if backscale else 0, nthreads)
+        return dict(U=U, V=V, smax=smax, smin=smin, s=s, wide=wide, count=int(cnt))
 
 
     def truth(self, A, s=None):
@@ -321,6 +342,10 @@ def svd2(A, *, backscale: bool = False, nthreads: int = 0):
 
 def svd2_rerun(A, tau_log2: int, *, backscale: bool = False, nthreads: int = 0):
     return _default().svd2_rerun(A, tau_log2, backscale=backscale, nthreads=nthreads)
+
+
+def svd2_tan64(A, tau_log2: int, *, backscale: bool = False, nthreads: int = 0):
+    return _default().svd2_tan64(A, tau_log2, backscale=backscale, nthreads=nthreads)
 
 
 def truth(A, s=None):

@@ -113,7 +113,11 @@ _Static_assert(LDBL_MANT_DIG == 113, "AArch64 long double must be binary128");
 #define T_COPYSIGN copysignf
 #define T_LOGB logbf
 #define T_SCALBN scalbnf
+#define T_WIDE double
+#define T_WIDE_FMA fma
 #include "svd2_oracle_body.h"
+#undef T_WIDE
+#undef T_WIDE_FMA
 #undef T
 #undef SFX
 #undef T_MAX
@@ -345,6 +349,44 @@ int64_t svd2o_batch_s_rerun(int64_t n, const float *const A[4], float *const U[4
             backscale_f(&sx, &sn, &so);
         smax[k] = sx; smin[k] = sn; s[k] = so;
         if (flagged) flagged[k] = (uint8_t)flag;
+    }
+    return count;
+}
+
+/*
+ * FP32 form with the FP64 tangent step (the precision variant of the
+ * single-precision remark of Sec. 1 and Sec. 7 that keeps double precision
+ * only where the method's stability needs it).  Every matrix is decomposed in
+ * float; a matrix with |r''_22| < 2^tau_log2 r11 at Eq. 7 has -tan(alpha) and
+ * the fma of Eq. 7 evaluated in double (svd2_real_t with T_WIDE = double).  In
+ * the real case every value that enters that fma is exact in float, so its
+ * double result is the double method's r''_22 / cos(alpha), up to the power of
+ * two between the two scales of Eq. 2, whenever both take the same pivots;
+ * it is the cancellation of Eq. 7 that costs sigma_min its accuracy in float.
+ * wide[k] (may be NULL) receives 1 for the matrices that took the step.
+ * Returns their count.
+ */
+int64_t svd2o_batch_s_tan64(int64_t n, const float *const A[4], float *const U[4],
+                            float *const V[4], float *smax, float *smin, int32_t *s,
+                            uint8_t *wide, int tau_log2, uint32_t flags, int nthreads)
+{
+    set_threads(nthreads);
+    int64_t count = 0;
+    const float tau = ldexpf(1.0f, tau_log2);
+#pragma omp parallel for schedule(static) reduction(+ : count)
+    for (int64_t k = 0; k < n; ++k) {
+        float a[2][2] = { { A[0][k], A[2][k] }, { A[1][k], A[3][k] } };
+        float u[2][2], v[2][2], sx, sn, sc;
+        int p, w;
+        svd2_real_t_s(a, u, v, &sx, &sn, &sc, &p, tau, &w);
+        U[0][k] = u[0][0]; U[1][k] = u[1][0]; U[2][k] = u[0][1]; U[3][k] = u[1][1];
+        V[0][k] = v[0][0]; V[1][k] = v[1][0]; V[2][k] = v[0][1]; V[3][k] = v[1][1];
+        int32_t so = s_to_i32_s(sc);
+        if (flags & SVD2O_BACKSCALE)
+            backscale_f(&sx, &sn, &so);
+        smax[k] = sx; smin[k] = sn; s[k] = so;
+        if (wide) wide[k] = (uint8_t)w;
+        count += w;
     }
     return count;
 }

@@ -106,8 +106,32 @@ static inline T SFX(scalef)(T a, T s)
  * exponent s (Eq. 2) and the two pivot bits (bit 0: P_c swapped the columns,
  * bit 1: P_r* swapped the rows).
  */
+static inline void SFX(svd2_real_t)(const T A[2][2], T U[2][2], T V[2][2],
+                           T *smax, T *smin, T *s_out, int *piv, T tau, int *wide);
+
 static inline void SFX(svd2_real)(const T A[2][2], T U[2][2], T V[2][2],
                            T *smax, T *smin, T *s_out, int *piv)
+{
+    int wide;
+    SFX(svd2_real_t)(A, U, V, smax, smin, s_out, piv, (T)0, &wide);
+}
+
+/*
+ * The same with the tangent step of Eq. 6 - Eq. 7 optionally taken in the next
+ * wider precision T_WIDE (defined for float only: the FP32 form with the FP64
+ * tangent step).  When |r''_22| < tau r11 -- evaluated in T; r''_22 / r11 is
+ * within a factor of two of sigma_min / sigma_max, because r11 <= sigma_max <=
+ * sqrt(2) r11 after the column pivoting and sigma_max sigma_min = r11 r22 --
+ * the quotient -tan(alpha) = pmax(a'''_21 / a'''_11, 0) and the fma of Eq. 7
+ * are evaluated again in T_WIDE on the exactly widened a''' (in the real case
+ * these are the scaled entries themselves, signs changed, so they are exact
+ * in T), and r''_22 = RN_T(cos(alpha) RN_T(fma_W(tan(alpha), a'''_12, a'''_22))),
+ * with the T value of cos(alpha).  Every other step stays in T.  *wide = 1
+ * when the step ran.  tau = 0 never runs it (|r''_22| < 0 is false): that is
+ * the plain method.
+ */
+static inline void SFX(svd2_real_t)(const T A[2][2], T U[2][2], T V[2][2],
+                           T *smax, T *smin, T *s_out, int *piv, T tau, int *wide)
 {
     /* Phase 1, Sec. 2.1: scale A by 2^s (Eq. 2, Fig. 3). */
     const T parts[4] = { A[0][0], A[1][0], A[0][1], A[1][1] };
@@ -160,7 +184,19 @@ static inline void SFX(svd2_real)(const T A[2][2], T U[2][2], T V[2][2],
     const T tana = -mtana;
     const T cosa = SFX(invsqrt)(T_FMA(tana, tana, (T)1));
     const T r12p = cosa * T_FMA(mtana, A3[1][1], A3[0][1]);  /* r'_12 */
-    const T r22pp = cosa * T_FMA(tana, A3[0][1], A3[1][1]);  /* r''_22: -(-tan a * a12) + a22 */
+    T r22pp = cosa * T_FMA(tana, A3[0][1], A3[1][1]);        /* r''_22: -(-tan a * a12) + a22 */
+    *wide = 0;
+#ifdef T_WIDE
+    if (T_FABS(r22pp) < tau * r11) {
+        const T_WIDE q = (T_WIDE)A3[1][0] / (T_WIDE)A3[0][0];
+        const T_WIDE mtw = q > (T_WIDE)0 ? q : (T_WIDE)0;       /* pmax(q, 0) */
+        const T_WIDE g = T_WIDE_FMA(-mtw, (T_WIDE)A3[0][1], (T_WIDE)A3[1][1]);
+        r22pp = cosa * (T)g;
+        *wide = 1;
+    }
+#else
+    (void)tau;
+#endif
 
     /* D~ of Eq. 8 and D^* of Eq. 9, real case (Eq. 10, Fig. 9). */
     const T dt = T_COPYSIGN((T)1, r12p);     /* d~_22 */

@@ -16,8 +16,17 @@ SRC = open(os.path.join(HERE, "svd2_oracle.c")).read()
 BODY = open(os.path.join(HERE, "svd2_oracle_body.h")).read()
 
 MUTATIONS = {
-    "r22_sign": ("const T r22pp = cosa * T_FMA(tana, A3[0][1], A3[1][1]);",
-                 "const T r22pp = cosa * T_FMA(mtana, A3[0][1], A3[1][1]);"),
+    "r22_sign": ("T r22pp = cosa * T_FMA(tana, A3[0][1], A3[1][1]);",
+                 "T r22pp = cosa * T_FMA(mtana, A3[0][1], A3[1][1]);"),
+    # the FP64 tangent step of the FP32 form (Eq. 6 - Eq. 7 in double)
+    "wide_quotient_in_float": ("const T_WIDE q = (T_WIDE)A3[1][0] / (T_WIDE)A3[0][0];",
+                               "const T_WIDE q = (T_WIDE)(A3[1][0] / A3[0][0]);"),
+    "wide_fma_sign": ("T_WIDE_FMA(-mtw, (T_WIDE)A3[0][1], (T_WIDE)A3[1][1]);",
+                      "T_WIDE_FMA(mtw, (T_WIDE)A3[0][1], (T_WIDE)A3[1][1]);"),
+    "wide_operands_swapped": ("T_WIDE_FMA(-mtw, (T_WIDE)A3[0][1], (T_WIDE)A3[1][1]);",
+                              "T_WIDE_FMA(-mtw, (T_WIDE)A3[1][1], (T_WIDE)A3[0][1]);"),
+    "wide_test_reversed": ("if (T_FABS(r22pp) < tau * r11) {", "if (T_FABS(r22pp) > tau * r11) {"),
+    "wide_cos_dropped": ("r22pp = cosa * (T)g;", "r22pp = (T)g;"),
     "u21_sign": ("Ur[1][0] = -(c * (d[1] * T_FMA(dh, tanp, tana)));",
                  "Ur[1][0] = (c * (d[1] * T_FMA(dh, tanp, tana)));"),
     "tanpsi_transposed": ("const T tanq = T_FMA(y, tanp, -x);",
@@ -68,6 +77,22 @@ def pin_failures(o):
             emax = e.max(axis=0)
             if not np.array_equal(r["s"].astype(np.int64), 1021 - emax):
                 failed.append(f"s{rows}")
+        # the FP32 form with the FP64 tangent step: sigma_min of the matrices that
+        # take it against the binary128 closed form (kappa <= 2^24), the trigger
+        # against sigma_min / sigma_max, sigma_max throughout
+        A32, _ = inputs.real_fp32_illcond(20000, seed=903)
+        r = o.svd2_tan64(A32, -4)
+        A64 = A32.astype(np.float64)
+        sxh, sxl, snh, snl = o.truth(A64, r["s"])
+        u = 2.0**-24
+        ex = np.abs((r["smax"].astype(np.float64) - sxh) - sxl) / sxh / u
+        en = np.abs((r["smin"].astype(np.float64) - snh) - snl) / snh / u
+        ratio = (snh + snl) / (sxh + sxl)
+        w = r["wide"].astype(bool)
+        sel = w & (ratio >= 2.0**-24)
+        if not (np.nanmax(ex) <= 8 and sel.any() and np.nanmax(en[sel]) <= 8
+                and np.all(w[ratio < 2.0**-5 * 0.999]) and not np.any(w & (ratio > 2.0**-4 * 1.001))):
+            failed.append("tan64")
         for row in read_rows("hand_cases.txt"):
             fields = dict(tok.split("=") for tok in row[1:])
             A = np.array([[hexf(t)] for t in fields["A"].split(",")])

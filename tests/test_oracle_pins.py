@@ -476,3 +476,78 @@ def test_generators_shapes_and_classes():
     lens, cplx = inputs.kog_batches()
     assert lens.size == 2048 and lens.min() >= 16 and lens.max() <= 2**20
     assert np.array_equal(inputs.normal_batch(10, 4, 5), inputs.normal_batch(10, 4, 5))
+
+
+# -------------------------------------- FP32 form with the FP64 tangent step
+
+def _tan64_truth_errors(o, A32, tau):
+    """Relative errors, in units of 2^-24, of the FP32-with-FP64-tangent form
+    (oracle build ``o``) against the binary128 closed form of the float input
+    (sigma_max, sigma_min) and against the pinned double method (sigma_min),
+    plus the exact sigma_min / sigma_max and the form's own result."""
+    u = 2.0**-24
+    r = o.svd2_tan64(A32, tau)
+    A64 = A32.astype(np.float64)
+    sxh, sxl, snh, snl = o.truth(A64, r["s"])
+    with np.errstate(all="ignore"):
+        ex = np.abs((r["smax"].astype(np.float64) - sxh) - sxl) / sxh / u
+        en = np.abs((r["smin"].astype(np.float64) - snh) - snl) / snh / u
+        d = o.svd2(A64, backscale=True)
+        back = np.ldexp(r["smin"].astype(np.float64), -r["s"])
+        e64 = np.abs(back - d["smin"]) / d["smin"] / u
+        ratio = (snh + snl) / (sxh + sxl)
+    return r, ex, en, e64, ratio
+
+
+def test_tan64_form_pins():
+    """The FP32 form that evaluates the tangent step of Eq. 6 - Eq. 7 in double
+    when |r''_22| < 2^tau r11:
+    - matrices that do not take the step are the plain float method bit for bit;
+    - the step's trigger brackets sigma_min / sigma_max: every matrix below
+      2^(tau-1) takes it, none above 2^tau does (r11 <= sigma_max <= sqrt(2) r11
+      and sigma_max sigma_min = r11 r22, so r22 / r11 is within a factor 2);
+    - in the real case only the quotient tan(alpha) is rounded before the
+      cancellation of Eq. 7, so with it in double sigma_min is as accurate as
+      float can hold wherever the double method is: within 8 units of 2^-24 of
+      the binary128 closed form up to kappa = 2^24 (the double method's own
+      error there is below 2^-29), and within 8 units of the double method at
+      every kappa of the batch (up to 10^12)."""
+    A32, ill = inputs.real_fp32_illcond(60000, seed=2024)
+    tau = -4
+    r, ex, en, e64, ratio = _tan64_truth_errors(oracle._default(), A32, tau)
+    w = r["wide"].astype(bool)
+    assert r["count"] == int(w.sum())
+    p = oracle.svd2(A32)
+    for k in ("U", "V", "smax", "smin"):
+        assert bits_equal(r[k][..., ~w], p[k][..., ~w]), k
+    assert np.array_equal(r["s"], p["s"])
+    assert np.all(w[ratio < 2.0**(tau - 1) * 0.999])
+    assert not np.any(w & (ratio > 2.0**tau * 1.001))
+    assert np.nanmax(ex) <= 8
+    kappa = 1 / ratio
+    sel = w & (kappa <= 2.0**24)
+    assert sel.sum() > 1000 and en[sel].max() <= 8
+    assert (w & (kappa > 2.0**30)).sum() > 500
+    assert e64[w].max() <= 8
+    # without the step the same matrices lose sigma_min entirely
+    _, _, en0, _, _ = _tan64_truth_errors(oracle._default(), A32, -200)
+    assert en0[w & (kappa > 2.0**20)].max() > 1e3
+
+
+def test_tan64_threshold_zero_and_extremes():
+    """tau = 0 runs the step wherever r''_22 < r11, i.e. on every matrix but the
+    zero matrix and those with r''_22 = r11; at tau = -200 it never runs and the
+    form is the plain float method."""
+    A = inputs.normal_batch(4096, 4, 77, np.float32)
+    A[:, :16] = 0                                          # zero matrices
+    A[1, 16:32] = 0                                        # upper triangular
+    A[:, 32:48] = inputs.random_bits_f32(16, 4, seed=78)   # the paper's random-bit class
+    r0 = oracle.svd2_tan64(A, -200)
+    p = oracle.svd2(A)
+    assert r0["count"] == 0
+    for k in ("U", "V", "smax", "smin", "s"):
+        assert bits_equal(r0[k], p[k]) if k != "s" else np.array_equal(r0[k], p[k])
+    r1 = oracle.svd2_tan64(A, 0)
+    zero = np.all(A == 0, axis=0)
+    assert not r1["wide"][zero].any()
+    assert r1["count"] > 0.9 * A.shape[1]
