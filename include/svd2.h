@@ -208,6 +208,34 @@ int svd2_batch_c_rerun(int64_t n, const float *const A[8], float *const U[8],
 int svd2_rerun_count(const void *workspace, int64_t *count);
 
 /*
+ * Real FP32 form with the FP64 tangent step.  The single-precision method (as
+ * svd2_batch_s) runs over all n matrices, and where a matrix is
+ * ill-conditioned one step of it runs in double precision: when
+ * |r''_22| < 2^tau_log2 * r11 at Eq. 7 (compared in float; r''_22 / r11 is
+ * within a factor of two of sigma_min / sigma_max, since r11 <= sigma_max <=
+ * sqrt(2) r11 after the column pivoting of Fig. 5), the quotient
+ * -tan(alpha) = a'''_21 / a'''_11 of Eq. 6 and the fma of Eq. 7 are evaluated
+ * in double on the exactly widened a''' and
+ * r''_22 = RN32(cos(alpha) * RN32(fma64(tan(alpha), a'''_12, a'''_22))).
+ * Every other step stays in float.  In the real case the a''' are the
+ * scaled entries with their signs changed, so they are exact in float and
+ * the cancellation of Eq. 7 -- where single precision loses the small
+ * singular value of an ill-conditioned matrix (Fig. 8) -- is the double
+ * method's own.  Matrices that do not take the step get exactly the
+ * svd2_batch_s results.  tau_log2 in [-100, 0]; SVD2_TAN64_TAU_LOG2 is the
+ * library's measured default.  count: NULL, or a device uint64 to which the
+ * call ADDS the number of matrices that took the step (zero it first).  One
+ * kernel and the fix-up pass on the stream; no workspace.  Other arguments,
+ * results and errors as svd2_batch_s (the paper reports no single-precision
+ * results; Sec. 1 and Sec. 7 remark on single precision).
+ */
+#define SVD2_TAN64_TAU_LOG2 (-3)
+int svd2_batch_s_tan64(int64_t n, const float *const A[4], float *const U[4],
+                       float *const V[4], float *smax, float *smin, int32_t *s,
+                       int tau_log2, uint32_t flags, unsigned long long *count,
+                       svd2_stream_t stream);
+
+/*
  * svd2_batch_s_rerun without a workspace argument, for callers that cannot
  * allocate device memory: an application whose device memory belongs to
  * another allocator (a framework's caching pool, or a host program that gives
@@ -221,7 +249,9 @@ int svd2_rerun_count(const void *workspace, int64_t *count);
  * process exits; n is limited to SVD2_NOALLOC_MAX_N matrices (larger n returns
  * SVD2_ETOOBIG) -- split larger batches, or use svd2_batch_s_rerun.  The first
  * call on a device (with that device current) looks up the array's address;
- * make it before any stream capture.  The call allocates nothing.  All calls
+ * make it before any stream capture.  The address is kept for the life of the
+ * process, so the entry point must not be used on a device after
+ * cudaDeviceReset (which may reload the library's device code elsewhere).  The call allocates nothing.  All calls
  * on one device share the array: calls whose GPU work may overlap (different
  * streams with no ordering between them) race and must not be made.
  * Arguments, results and other errors as svd2_batch_s_rerun.
@@ -240,7 +270,8 @@ int svd2_batch_s_rerun_noalloc(int64_t n, const float *const A[4], float *const 
  *   a = J12 - J21,  b = K12 - K21,  p = (a-b)/(2(s1+s2)),  q = (a+b)/(2(s1-s2)),
  * with 1/(s1 - s2) replaced by g / (s1 (g^2 + rel_delta^2)), g = (s1 - s2)/s1,
  * which equals it for g >> rel_delta and stays bounded as the singular values
- * meet (rel_delta >= 0; 0 disables the safeguard).  s1, s2 are the singular
+ * meet (rel_delta >= 0; 0 disables the safeguard, except that s1 = s2, where
+ * the formula reads 0/0, gives the safeguard's value at zero gap, 0).  s1, s2 are the singular
  * values themselves (back-scaled: a forward call with SVD2_BACKSCALE).  U, V,
  * s1, s2 as produced by svd2_batch_d / svd2_batch_s.  gU, gV may be NULL (and
  * their entries, g1, g2) to mean zero gradients.  Device arrays of n values,
@@ -296,7 +327,9 @@ int svd2_bwd_c(int64_t n, const float *const U[8], const float *const V[8],
  * svd2_multi_run: one launch per kind over the plan, then the fix-up pass
  *   over every batch (reads the plan's flag word and ends when nothing was
  *   marked), asynchronous on `stream`; block, mpt and unroll must be those of
- *   the plan (otherwise the launch does nothing).  grid 0: one block per tile for a plan prepared in
+ *   the plan: for a plan prepared in this process another tile size returns
+ *   SVD2_EINVAL (a plan copied in from elsewhere is checked by the kernels,
+ *   which then process nothing).  grid 0: one block per tile for a plan prepared in
  *   this process (the tile counts are remembered on the host; the fastest on
  *   GB300), else SMs x resident blocks; grid > 0: that many blocks, a
  *   persistent grid walking the tiles when it is at most the resident count.
@@ -351,7 +384,8 @@ int svd2_multi_autotune(const svd2_batch_desc *descs, int32_t nbatch, void *plan
                         svd2_stream_t stream);
 
 /*
- * The forward forms (op 0 = d, 1 = z, 2 = s, 3 = c) on a batch held in HOST
+ * The forward forms (op 0 = d, 1 = z, 2 = s, 3 = c, 4 = svd2_batch_s_tan64 at
+ * SVD2_TAN64_TAU_LOG2) on a batch held in HOST
  * memory: A, U, V are host arrays of host element pointers, smax, smin, s host
  * arrays, in the layout above.  When every array is page-locked host memory
  * (cudaHostAlloc, cudaMallocHost, cudaHostRegister; checked with

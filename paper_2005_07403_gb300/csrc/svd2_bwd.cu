@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs<T> p) {
     T inv_gap = T(0);
     if (s1 > T(0)) {
       const T g = F::div(F::sub(s1, s2), s1);
-      inv_gap = F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
+      // g = 0: the safeguard's value there (0), also for rel_delta = 0 (0/0)
+      inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
     }
     const T pp = F::mul(F::mul(T(0.5), F::sub(a, b)), inv_sum);
     const T qq = F::mul(F::mul(T(0.5), F::add(a, b)), inv_gap);
@@ -159,7 +160,8 @@ __global__ void __launch_bounds__(256) bwd_cplx_kernel(const BwdArgsC<T> p) {
     T inv_gap = T(0);
     if (s1 > T(0)) {
       const T g = F::div(F::sub(s1, s2), s1);
-      inv_gap = F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
+      // g = 0: the safeguard's value there (0), also for rel_delta = 0 (0/0)
+      inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
     }
     const T pr = F::mul(F::mul(T(0.5), F::sub(ar, br)), inv_sum);
     const T pi = F::mul(F::mul(T(0.5), F::sub(ai, bi)), inv_sum);

@@ -25,7 +25,8 @@ struct FwdArgs {
   int32_t *s;
   int64_t n;
   uint32_t flags;
-  // FP32 form with FP64 re-run only: re-run threshold and re-run counter.
+  // FP32 forms with FP64 re-run or FP64 tangent step only: the threshold and
+  // the counter of the matrices that took the double-precision work.
   T tau;
   unsigned long long *count;
   // Set to nonzero by the fast kernel when it flagged a matrix (see fix_kernel).
@@ -118,23 +119,34 @@ __device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u
 // MARK (first pass of the FP32 form with re-run): a matrix whose
 // single-precision sigma' ask for the double-precision re-run gets
 // s = kRerunMark.
-template <typename T, bool CPLX, int M, bool VALS = false, bool MARK = false>
-__device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p, int64_t k0,
-                                              const T (&in)[CPLX ? 8 : 4][M]) {
+// TAN64 (real FP32 form with the FP64 tangent step): the tangent step of
+// Eq. 6 - Eq. 7 in double where |r''_22| < p.tau r11; returns the number of
+// matrices (not flagged for the fix-up pass) that took it.
+template <typename T, bool CPLX, bool TAN64>
+struct GroupArOf { using type = HotAr<T, CPLX>; };
+template <>
+struct GroupArOf<float, false, true> { using type = Tan64Ar<HotAr<float, false>>; };
+
+template <typename T, bool CPLX, int M, bool VALS = false, bool MARK = false, bool TAN64 = false>
+__device__ __forceinline__ unsigned process_group(const FwdArgs<T, CPLX ? 8 : 4> &p, int64_t k0,
+                                                  const T (&in)[CPLX ? 8 : 4][M]) {
   constexpr int NA = CPLX ? 8 : 4;
   T uo[NA][M], vo[NA][M], sx[M], sn[M];
   int32_t so[M];
-  unsigned bad = 0;
+  unsigned bad = 0, nwide = 0;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     T a[NA], u[NA], v[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
-    HotAr<T, CPLX> ar;
+    typename GroupArOf<T, CPLX, TAN64>::type ar;
+    if constexpr (TAN64) ar.tau = p.tau;
     svd2_one<T, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
     bool mark = false;
     if constexpr (MARK) mark = sn[m] < fp<T>::mul(p.tau, sx[m]);
     if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
+    // (a matrix handed to the fix-up pass is counted there)
+    if constexpr (TAN64) nwide += ar.bad ? 0u : ar.wide;
     so[m] = ar.bad ? kRedoS : mark ? kRerunMark : so[m];
     bad |= ar.bad;
 #pragma unroll
@@ -153,6 +165,14 @@ __device__ __forceinline__ void process_group(const FwdArgs<T, CPLX ? 8 : 4> &p,
   store_vec<T, M>(p.smin + k0, sn);
   store_vec<int32_t, M>(p.s + k0, so);
   if (bad) *p.redo = 1;
+  return nwide;
+}
+
+// Adds each warp's count to *count (one atomic per warp); every lane of the
+// warp calls it.
+__device__ __forceinline__ void warp_count_add(unsigned long long *count, unsigned c) {
+  const unsigned t = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && t) atomicAdd(count, (unsigned long long)t);
 }
 
 // Fix-up pass after the fast kernel, on the same stream: if the fast kernel
@@ -181,13 +201,18 @@ inline unsigned fix_grid(int64_t n) {
 // FP64 kernels and the complex FP32 one are bound by arithmetic latency and
 // run best at 64 registers (32 warps per SM; complex FP32 at 76 registers
 // measured 5% slower); the real FP32 one may use up to 128 (capping it at 32
-// registers for full occupancy measured no faster).
-template <typename T, bool CPLX> constexpr int kMinBlocks = (sizeof(T) == 8 || CPLX) ? 2 : 1;
+// registers for full occupancy measured no faster), except with the FP64
+// tangent step, whose 76 registers at two matrices per thread left 16 warps
+// per SM: at 64 registers it runs 19% faster (56.2 -> 67.0 G matrices/s).
+template <typename T, bool CPLX, bool TAN64 = false>
+constexpr int kMinBlocks = (sizeof(T) == 8 || CPLX || TAN64) ? 2 : 1;
 
-template <typename T, bool CPLX, int M, int UNR, bool VALS = false, bool MARK = false>
-__global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
+template <typename T, bool CPLX, int M, int UNR, bool VALS = false, bool MARK = false,
+          bool TAN64 = false>
+__global__ void __launch_bounds__(512, (kMinBlocks<T, CPLX, TAN64>))
     fwd_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
+  unsigned nwide = 0;
   const int64_t ngroups = p.n / M;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,7 +229,7 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
       const int64_t g = g0 + r * stride;
-      if (g < ngroups) process_group<T, CPLX, M, VALS, MARK>(p, g * M, in[r]);
+      if (g < ngroups) nwide += process_group<T, CPLX, M, VALS, MARK, TAN64>(p, g * M, in[r]);
     }
   }
   // the n mod M tail, one matrix per thread
@@ -213,7 +238,10 @@ __global__ void __launch_bounds__(512, kMinBlocks<T, CPLX>)
     T in1[NA][1];
 #pragma unroll
     for (int e = 0; e < NA; ++e) in1[e][0] = p.a[e][k];
-    process_group<T, CPLX, 1, VALS, MARK>(p, k, in1);
+    nwide += process_group<T, CPLX, 1, VALS, MARK, TAN64>(p, k, in1);
+  }
+  if constexpr (TAN64) {
+    if (p.count) warp_count_add(p.count, nwide);
   }
 }
 

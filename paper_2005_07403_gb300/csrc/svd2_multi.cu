@@ -193,10 +193,15 @@ static MultiKernel pick_multi(int mpt, int unroll) {
 
 using namespace svd2;
 
-// Tile counts of the plans prepared in this process (real, complex), keyed by
-// the plan's device address: grid 0 launches one block per tile.
+// Tile counts of the plans prepared in this process (real, complex) and their
+// tile size (matrices per tile), keyed by the plan's device address: grid 0
+// launches one block per tile, and a launch shape with another tile size is
+// rejected.
+struct PlanTiles {
+  int64_t real, cplx, per_tile;
+};
 static std::mutex g_tiles_mu;
-static std::unordered_map<const void *, std::pair<int64_t, int64_t>> g_tiles;
+static std::unordered_map<const void *, PlanTiles> g_tiles;
 
 extern "C" size_t svd2_multi_plan_bytes(int32_t nbatch) {
   if (nbatch < 0) return 0;
@@ -268,7 +273,7 @@ extern "C" int svd2_multi_prepare(const svd2_batch_desc *descs, int32_t nbatch, 
   if (total_tiles) *total_tiles = tiles_of[0] + tiles_of[1];
   {
     std::lock_guard<std::mutex> g(g_tiles_mu);
-    g_tiles[plan] = {tiles_of[0], tiles_of[1]};
+    g_tiles[plan] = {tiles_of[0], tiles_of[1], per_tile};
   }
   return SVD2_OK;
 }
@@ -302,8 +307,10 @@ static int multi_launch(const void *plan, int block, int mpt, int unroll, int gr
     std::lock_guard<std::mutex> g(g_tiles_mu);
     auto it = g_tiles.find(plan);
     if (it != g_tiles.end()) {
-      tr = it->second.first;
-      tz = it->second.second;
+      // the kernels process nothing with another tile size than the plan's
+      if ((int64_t)block * mpt * unroll != it->second.per_tile) return SVD2_EINVAL;
+      tr = it->second.real;
+      tz = it->second.cplx;
     }
   }
   int gr = 0, gz = 0;

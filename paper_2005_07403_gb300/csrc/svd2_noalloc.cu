@@ -16,7 +16,10 @@
 //
 // Set-up: the first call on a device, with that device current, looks up the
 // array's device address with cudaGetSymbolAddress (no allocation) and caches
-// it; make that first call before any stream capture.  In host code the array's
+// it; make that first call before any stream capture.  The cached address
+// holds while the device's context lives: after cudaDeviceReset the module may
+// be loaded again at another address, so the entry point must not be used
+// across a device reset.  In host code the array's
 // name is only a host-side stand-in, so the kernels always receive the looked-up
 // address.  All calls on a device share the one array: the count, the flag and
 // the list length are cleared at the start of each call, and calls whose

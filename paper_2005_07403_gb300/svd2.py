@@ -102,6 +102,9 @@ def _declare(L):
         f.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int, ctypes.c_uint32, P,
                       ctypes.c_size_t, P]
         f.restype = ctypes.c_int
+    L.svd2_batch_s_tan64.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int,
+                                     ctypes.c_uint32, P, P]
+    L.svd2_batch_s_tan64.restype = ctypes.c_int
     L.svd2_batch_s_rerun_noalloc.argtypes = [ctypes.c_int64, PP, PP, PP, P, P, P, ctypes.c_int,
                                              ctypes.c_uint32, P]
     L.svd2_batch_s_rerun_noalloc.restype = ctypes.c_int
@@ -341,18 +344,22 @@ def empty_host_result(rows: int, n: int, dtype, pin: bool = True) -> Svd2Result:
 
 
 def svd2_host(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = None,
-              chunk: int = 0, device=None, stream: int | None = None) -> Svd2Result:
+              chunk: int = 0, device=None, stream: int | None = None,
+              tan64: bool = False) -> Svd2Result:
     """Forward form on a batch in host memory (svd2_batch_host): A is a CPU
     tensor (pinned for overlap) of shape (4, n) or (8, n); outputs are host
-    tensors.  Asynchronous on the device's current stream (or ``stream``):
-    synchronise before reading the outputs."""
+    tensors.  ``tan64``: the real FP32 form with the FP64 tangent step at the
+    default threshold.  Asynchronous on the device's current stream (or
+    ``stream``): synchronise before reading the outputs."""
     rows, n = A.shape
     kind = _kind(rows, A.dtype)
+    if tan64 and kind != "s":
+        raise TypeError("the FP64 tangent step form takes real float32 input")
     if out is None:
         out = empty_host_result(rows, n, A.dtype)
     dev = torch.device("cuda") if device is None else torch.device(device)
     h = current_stream_handle(dev) if stream is None else stream
-    rc = lib().svd2_batch_host(OPS[kind], n, ptr_array(_host_rows(A, "A")),
+    rc = lib().svd2_batch_host(HOST_OP_S_TAN64 if tan64 else OPS[kind], n, ptr_array(_host_rows(A, "A")),
                                ptr_array(_host_rows(out.U, "U")), ptr_array(_host_rows(out.V, "V")),
                                out.smax.data_ptr(), out.smin.data_ptr(), out.s.data_ptr(),
                                BACKSCALE if backscale else 0, int(chunk), h)
@@ -361,6 +368,35 @@ def svd2_host(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | Non
 
 
 RERUN_TAU_LOG2 = -8
+TAN64_TAU_LOG2 = -3
+HOST_OP_S_TAN64 = 4
+
+
+def svd2_tan64(A: torch.Tensor, *, tau_log2: int = TAN64_TAU_LOG2, backscale: bool = False,
+               out: Svd2Result | None = None, count: torch.Tensor | None = None,
+               stream: int | None = None) -> Svd2Result:
+    """Real FP32 form with the FP64 tangent step (svd2_batch_s_tan64) for the
+    matrices with |r''_22| < 2^tau_log2 r11.  ``A`` is float32 of shape (4, n).
+    ``count``: optional one-element int64 CUDA tensor to which the call adds
+    the number of matrices that took the step."""
+    rows, n = A.shape
+    if A.dtype != torch.float32 or rows != 4:
+        raise TypeError("svd2_tan64 takes real float32 input of shape (4, n)")
+    a_ptrs = _rows(A, "A")
+    if out is None:
+        out = empty_result(rows, n, A.dtype, A.device)
+    h = current_stream_handle(A.device) if stream is None else stream
+    cp = None
+    if count is not None:
+        if count.dtype != torch.int64 or count.numel() != 1 or not count.is_cuda:
+            raise TypeError("count must be a one-element int64 CUDA tensor")
+        cp = count.data_ptr()
+    rc = lib().svd2_batch_s_tan64(n, ptr_array(a_ptrs), ptr_array(_rows(out.U, "U")),
+                                  ptr_array(_rows(out.V, "V")), out.smax.data_ptr(),
+                                  out.smin.data_ptr(), out.s.data_ptr(), int(tau_log2),
+                                  BACKSCALE if backscale else 0, cp, h)
+    check(rc, "svd2_batch_s_tan64")
+    return out
 
 
 def rerun_workspace(n: int, device="cuda") -> torch.Tensor:

@@ -60,6 +60,25 @@ def test_bwd_matches_oracle_adjoint_bitwise(dt, tdt):
     assert bits_equal(gA.cpu().numpy(), o)
 
 
+@pytest.mark.parametrize("rows", [4, 8])
+@pytest.mark.parametrize("dt,tdt", [(np.float64, torch.float64), (np.float32, torch.float32)])
+def test_bwd_equal_singular_values_without_safeguard(rows, dt, tdt):
+    """rel_delta = 0 with s1 = s2: the rotation term takes the safeguard's
+    value at zero gap (0), not 0/0; gA is finite and equal to the oracle's."""
+    rng = np.random.default_rng(91)
+    n = 4099
+    U, V = rng.standard_normal((2, rows, n)).astype(dt)
+    s = (np.abs(rng.standard_normal(n)) + 0.5).astype(dt)
+    gU, gV = rng.standard_normal((2, rows, n)).astype(dt)
+    g1, g2 = rng.standard_normal((2, n)).astype(dt)
+    gA = S.svd2_bwd(_dev(U, tdt), _dev(V, tdt), _dev(s, tdt), _dev(s, tdt), _dev(gU, tdt),
+                    _dev(gV, tdt), _dev(g1, tdt), _dev(g2, tdt), 0.0)
+    torch.cuda.synchronize()
+    g = gA.cpu().numpy()
+    assert np.all(np.isfinite(g))
+    assert bits_equal(g, oracle.bwd(U, V, s, s, gU, gV, g1, g2, 0.0))
+
+
 def test_bwd_null_gradients_are_zero():
     A, gU, gV, gS = _edge_and_batch(1000, np.float64)
     r = S.svd2(_dev(A), backscale=True)

@@ -1,6 +1,8 @@
 """The multi-batch launch (svd2_multi_*: one block per tile by default, or a
 persistent grid), its CUDA graph, and the autotuners, against the oracle
 batch by batch (bit for bit)."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -71,15 +73,24 @@ def test_multi_graph_replay_follows_data():
     g.close()
 
 
-def test_multi_shape_mismatch_does_nothing():
+def test_multi_shape_mismatch_is_rejected():
+    """A launch whose tile size (block x mpt x unroll) differs from the plan's
+    would process nothing: run and graph creation return SVD2_EINVAL and leave
+    the outputs untouched."""
     hosts = _batches(5, 5, lo=100, hi=500)
     mb = S.MultiBatch([torch.from_numpy(A).cuda() for A in hosts], 256, 1, 1)
     for o in mb.outputs:
         o.smax.fill_(7.0)
-    S.check(S.lib().svd2_multi_run(mb.plan.data_ptr(), 128, 1, 1, 0,
-                                   S.current_stream_handle()), "run")
+    L = S.lib()
+    assert L.svd2_multi_run(mb.plan.data_ptr(), 128, 1, 1, 0, S.current_stream_handle()) == S.EINVAL
+    assert L.svd2_multi_run(mb.plan.data_ptr(), 256, 2, 1, 0, S.current_stream_handle()) == S.EINVAL
+    h = ctypes.c_void_p()
+    assert L.svd2_multi_graph_create(mb.plan.data_ptr(), 128, 1, 1, 0, ctypes.byref(h)) == S.EINVAL
     torch.cuda.synchronize()
     assert all(bool(torch.all(o.smax == 7.0)) for o in mb.outputs)
+    # the plan's own shape still runs
+    assert L.svd2_multi_run(mb.plan.data_ptr(), 256, 1, 1, 0, S.current_stream_handle()) == S.OK
+    _check_all(mb, hosts, "after rejected shapes")
 
 
 def test_multi_autotune_picks_a_valid_shape():

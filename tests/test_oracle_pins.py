@@ -454,6 +454,26 @@ def test_adjoint_safeguard():
     assert np.allclose(gA[:, 0], [0.0, -1 / 6 - 0.5, 1 / 6 - 0.5, 0.0], rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("rows,dt", [(4, np.float64), (4, np.float32), (8, np.float64),
+                                     (8, np.float32)])
+def test_adjoint_equal_singular_values_without_safeguard(rows, dt):
+    """rel_delta = 0 turns the safeguard off, where g / (s1 (g^2 + 0)) reads 0/0
+    at s1 = s2 (a multiple of an orthogonal or unitary matrix).  The adjoint
+    then takes the value the safeguard has at g = 0 for every rel_delta > 0,
+    namely 0 for the rotation term: finite, and bit-identical to rel_delta > 0."""
+    rng = np.random.default_rng(7)
+    n = 64
+    U = rng.standard_normal((rows, n)).astype(dt)
+    V = rng.standard_normal((rows, n)).astype(dt)
+    s = np.abs(rng.standard_normal(n)).astype(dt) + dt(0.5)
+    gU, gV = rng.standard_normal((2, rows, n)).astype(dt)
+    g1, g2 = rng.standard_normal((2, n)).astype(dt)
+    a0 = oracle.bwd(U, V, s, s, gU, gV, g1, g2, 0.0)
+    a1 = oracle.bwd(U, V, s, s, gU, gV, g1, g2, 1e-3)
+    assert np.all(np.isfinite(a0))
+    assert bits_equal(a0, a1)
+
+
 # ----------------------------------------------------------- the generators
 
 def test_generators_shapes_and_classes():
