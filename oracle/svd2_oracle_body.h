@@ -417,7 +417,9 @@ static inline void SFX(adjoint)(const T u[4], const T v[4], T s1, T s2, const T 
     T inv_gap = (T)0;
     if (s1 > (T)0) {
         const T g = (s1 - s2) / s1;
-        inv_gap = g / (s1 * (g * g + dl * dl));
+        /* g = 0 (s1 = s2): the safeguard's value there, 0, also at dl = 0,
+         * where the formula reads 0/0 */
+        inv_gap = g == (T)0 ? (T)0 : g / (s1 * (g * g + dl * dl));
     }
     const T p = (T)0.5 * (a - b) * inv_sum;
     const T q = (T)0.5 * (a + b) * inv_gap;
@@ -474,7 +476,9 @@ static inline void SFX(adjoint_cplx)(const T ur[4], const T ui[4], const T vr[4]
     T inv_gap = (T)0;
     if (s1 > (T)0) {
         const T g = (s1 - s2) / s1;
-        inv_gap = g / (s1 * (g * g + dl * dl));
+        /* g = 0 (s1 = s2): the safeguard's value there, 0, also at dl = 0,
+         * where the formula reads 0/0 */
+        inv_gap = g == (T)0 ? (T)0 : g / (s1 * (g * g + dl * dl));
     }
     const T pr = (T)0.5 * (ar - br) * inv_sum, pi = (T)0.5 * (ai - bi) * inv_sum;
     const T qr = (T)0.5 * (ar + br) * inv_gap, qi = (T)0.5 * (ai + bi) * inv_gap;
