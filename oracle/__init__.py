@@ -31,6 +31,7 @@ LIB_PATH = os.path.join(BUILD_DIR, "libsvd2_oracle.so")
 
 ZERO_S = 2**31 - 1
 BACKSCALE = 1
+SINE = 2          # U by Eq. 31 (sines) instead of Eq. 29 (tangents)
 
 _lock = threading.Lock()
 _lib = None
@@ -148,13 +149,15 @@ class Oracle:
         return self.lib.svd2o_max_threads()
 
 
-    def svd2(self, A, *, backscale: bool = False, nthreads: int = 0):
+    def svd2(self, A, *, backscale: bool = False, sine: bool = False, nthreads: int = 0):
         """Step oracle O1 (Sec. 2 - Sec. 7, Eq. 29) over a batch.
 
         ``A`` has shape (4, n) (real) or (8, n) (complex), dtype float64 or float32;
         the precision of the method is the dtype's.  Returns a dict with U, V (same
         shape as A), smax, smin (scaled, Eq. 17, unless backscale), s (int32) and
-        piv (uint8; bit 0 = column swap P_c, bit 1 = row swap P_r*).
+        piv (uint8; bit 0 = column swap P_c, bit 1 = row swap P_r*).  ``sine``: U
+        assembled by Eq. 31 from the sines sin = cos tan (Sec. 7) instead of
+        the tangent form of Eq. 29.
         """
         A = np.asarray(A)
         rows = A.shape[0]
@@ -173,7 +176,7 @@ class Oracle:
         name = {(4, np.float64): "svd2o_batch_d", (4, np.float32): "svd2o_batch_s",
                 (8, np.float64): "svd2o_batch_z", (8, np.float32): "svd2o_batch_c"}[(rows, dt)]
         getattr(lib, name)(n, _ptrs(A), _ptrs(U), _ptrs(V), _p(smax), _p(smin), _p(s), _p(piv),
-                           BACKSCALE if backscale else 0, nthreads)
+                           (BACKSCALE if backscale else 0) | (SINE if sine else 0), nthreads)
         return dict(U=U, V=V, smax=smax, smin=smin, s=s, piv=piv)
 
 
@@ -336,8 +339,8 @@ def max_threads():
     return _default().max_threads()
 
 
-def svd2(A, *, backscale: bool = False, nthreads: int = 0):
-    return _default().svd2(A, backscale=backscale, nthreads=nthreads)
+def svd2(A, *, backscale: bool = False, sine: bool = False, nthreads: int = 0):
+    return _default().svd2(A, backscale=backscale, sine=sine, nthreads=nthreads)
 
 
 def svd2_rerun(A, tau_log2: int, *, backscale: bool = False, nthreads: int = 0):

@@ -172,6 +172,8 @@ int svd2o_max_threads(void)
 
 /* Fig. 1: optional backscaling Sigma = 2^-s Sigma', after which s reads 0. */
 #define SVD2O_BACKSCALE 1u
+/* U assembled by Eq. 31 (sines and cosines) instead of Eq. 29 (tangents). */
+#define SVD2O_SINE 2u
 
 /* ----------------------------------------------- O1 batch entry points ---- */
 /*
@@ -191,7 +193,8 @@ void svd2o_batch_d(int64_t n, const double *const A[4], double *const U[4],
         double a[2][2] = { { A[0][k], A[2][k] }, { A[1][k], A[3][k] } };
         double u[2][2], v[2][2], sx, sn, sc;
         int p;
-        svd2_real_d(a, u, v, &sx, &sn, &sc, &p);
+        int w;
+        svd2_real_t_d(a, u, v, &sx, &sn, &sc, &p, 0.0, &w, (flags & SVD2O_SINE) != 0);
         U[0][k] = u[0][0]; U[1][k] = u[1][0]; U[2][k] = u[0][1]; U[3][k] = u[1][1];
         V[0][k] = v[0][0]; V[1][k] = v[1][0]; V[2][k] = v[0][1]; V[3][k] = v[1][1];
         int32_t si = s_to_i32_d(sc);
@@ -216,7 +219,8 @@ void svd2o_batch_s(int64_t n, const float *const A[4], float *const U[4],
         float a[2][2] = { { A[0][k], A[2][k] }, { A[1][k], A[3][k] } };
         float u[2][2], v[2][2], sx, sn, sc;
         int p;
-        svd2_real_s(a, u, v, &sx, &sn, &sc, &p);
+        int w;
+        svd2_real_t_s(a, u, v, &sx, &sn, &sc, &p, 0.0f, &w, (flags & SVD2O_SINE) != 0);
         U[0][k] = u[0][0]; U[1][k] = u[1][0]; U[2][k] = u[0][1]; U[3][k] = u[1][1];
         V[0][k] = v[0][0]; V[1][k] = v[1][0]; V[2][k] = v[0][1]; V[3][k] = v[1][1];
         int32_t si = s_to_i32_s(sc);
@@ -242,7 +246,7 @@ void svd2o_batch_z(int64_t n, const double *const A[8], double *const U[8],
         double ai[2][2] = { { A[1][k], A[5][k] }, { A[3][k], A[7][k] } };
         double ur[2][2], ui[2][2], vr[2][2], vi[2][2], sx, sn, sc;
         int p;
-        svd2_cplx_d(ar, ai, ur, ui, vr, vi, &sx, &sn, &sc, &p);
+        svd2_cplx_t_d(ar, ai, ur, ui, vr, vi, &sx, &sn, &sc, &p, (flags & SVD2O_SINE) != 0);
         for (int j = 0; j < 2; ++j)
             for (int i = 0; i < 2; ++i) {
                 const int e = 2 * (2 * j + i);   /* element (i,j) -> record slot */
@@ -272,7 +276,7 @@ void svd2o_batch_c(int64_t n, const float *const A[8], float *const U[8],
         float ai[2][2] = { { A[1][k], A[5][k] }, { A[3][k], A[7][k] } };
         float ur[2][2], ui[2][2], vr[2][2], vi[2][2], sx, sn, sc;
         int p;
-        svd2_cplx_s(ar, ai, ur, ui, vr, vi, &sx, &sn, &sc, &p);
+        svd2_cplx_t_s(ar, ai, ur, ui, vr, vi, &sx, &sn, &sc, &p, (flags & SVD2O_SINE) != 0);
         for (int j = 0; j < 2; ++j)
             for (int i = 0; i < 2; ++i) {
                 const int e = 2 * (2 * j + i);
@@ -378,7 +382,7 @@ int64_t svd2o_batch_s_tan64(int64_t n, const float *const A[4], float *const U[4
         float a[2][2] = { { A[0][k], A[2][k] }, { A[1][k], A[3][k] } };
         float u[2][2], v[2][2], sx, sn, sc;
         int p, w;
-        svd2_real_t_s(a, u, v, &sx, &sn, &sc, &p, tau, &w);
+        svd2_real_t_s(a, u, v, &sx, &sn, &sc, &p, tau, &w, 0);
         U[0][k] = u[0][0]; U[1][k] = u[1][0]; U[2][k] = u[0][1]; U[3][k] = u[1][1];
         V[0][k] = v[0][0]; V[1][k] = v[1][0]; V[2][k] = v[0][1]; V[3][k] = v[1][1];
         int32_t so = s_to_i32_s(sc);

@@ -107,13 +107,14 @@ static inline T SFX(scalef)(T a, T s)
  * bit 1: P_r* swapped the rows).
  */
 static inline void SFX(svd2_real_t)(const T A[2][2], T U[2][2], T V[2][2],
-                           T *smax, T *smin, T *s_out, int *piv, T tau, int *wide);
+                           T *smax, T *smin, T *s_out, int *piv, T tau, int *wide,
+                           int sine);
 
 static inline void SFX(svd2_real)(const T A[2][2], T U[2][2], T V[2][2],
                            T *smax, T *smin, T *s_out, int *piv)
 {
     int wide;
-    SFX(svd2_real_t)(A, U, V, smax, smin, s_out, piv, (T)0, &wide);
+    SFX(svd2_real_t)(A, U, V, smax, smin, s_out, piv, (T)0, &wide, 0);
 }
 
 /*
@@ -128,10 +129,12 @@ static inline void SFX(svd2_real)(const T A[2][2], T U[2][2], T V[2][2],
  * in T), and r''_22 = RN_T(cos(alpha) RN_T(fma_W(tan(alpha), a'''_12, a'''_22))),
  * with the T value of cos(alpha).  Every other step stays in T.  *wide = 1
  * when the step ran.  tau = 0 never runs it (|r''_22| < 0 is false): that is
- * the plain method.
+ * the plain method.  sine != 0 assembles U by Eq. 31 instead of Eq. 29 (see
+ * below); V is the same either way.
  */
 static inline void SFX(svd2_real_t)(const T A[2][2], T U[2][2], T V[2][2],
-                           T *smax, T *smin, T *s_out, int *piv, T tau, int *wide)
+                           T *smax, T *smin, T *s_out, int *piv, T tau, int *wide,
+                           int sine)
 {
     /* Phase 1, Sec. 2.1: scale A by 2^s (Eq. 2, Fig. 3). */
     const T parts[4] = { A[0][0], A[1][0], A[0][1], A[1][1] };
@@ -231,6 +234,17 @@ static inline void SFX(svd2_real_t)(const T A[2][2], T U[2][2], T V[2][2],
     Ur[1][0] = -(c * (d[1] * T_FMA(dh, tanp, tana)));
     Ur[0][1] = c * (d[0] * T_FMA(dh, tana, tanp));
     Ur[1][1] = c * (d[1] * T_FMA(-tana, tanp, dh));
+    if (sine) {
+        /* Eq. 31: the same U from the sines and cosines, sin = cos tan
+         * (Sec. 7): pp = cos a cos p, qq = sin a sin p, rr = cos a sin p,
+         * tt = sin a cos p, each combined with d^_22 by one fma. */
+        const T sina = cosa * tana, sinp = cosp * tanp;
+        const T pp = cosa * cosp, qq = sina * sinp, rr = cosa * sinp, tt = sina * cosp;
+        Ur[0][0] = d[0] * T_FMA(-dh, qq, pp);
+        Ur[0][1] = d[0] * T_FMA(dh, tt, rr);
+        Ur[1][0] = -(d[1] * T_FMA(dh, rr, tt));
+        Ur[1][1] = d[1] * T_FMA(dh, pp, -qq);
+    }
     for (int i = 0; i < 2; ++i)              /* U = P_r (P_r* U) */
         for (int j = 0; j < 2; ++j)
             U[i][j] = Ur[pr ? 1 - i : i][j];
@@ -252,10 +266,22 @@ static inline void SFX(svd2_real_t)(const T A[2][2], T U[2][2], T V[2][2],
 /*
  * One complex 2x2 SVD, Sec. 2 (Eq. 1 - Eq. 29) as vectorized in Fig. 3 - Fig. 10,
  * one lane at a time.  Ar/Ai hold the real and imaginary parts of a_{i+1,j+1}.
+ * sine != 0 assembles U by Eq. 31 instead of Eq. 29 (V is the same).
  */
+static inline void SFX(svd2_cplx_t)(const T Ar[2][2], const T Ai[2][2],
+                           T Ur[2][2], T Ui[2][2], T Vr[2][2], T Vi[2][2],
+                           T *smax, T *smin, T *s_out, int *piv, int sine);
+
 static inline void SFX(svd2_cplx)(const T Ar[2][2], const T Ai[2][2],
                            T Ur[2][2], T Ui[2][2], T Vr[2][2], T Vi[2][2],
                            T *smax, T *smin, T *s_out, int *piv)
+{
+    SFX(svd2_cplx_t)(Ar, Ai, Ur, Ui, Vr, Vi, smax, smin, s_out, piv, 0);
+}
+
+static inline void SFX(svd2_cplx_t)(const T Ar[2][2], const T Ai[2][2],
+                           T Ur[2][2], T Ui[2][2], T Vr[2][2], T Vi[2][2],
+                           T *smax, T *smin, T *s_out, int *piv, int sine)
 {
     /* Phase 1: Eq. 2 over the real and the imaginary parts (Fig. 3). */
     const T parts[8] = { Ar[0][0], Ai[0][0], Ar[1][0], Ai[1][0],
@@ -365,6 +391,28 @@ static inline void SFX(svd2_cplx)(const T Ar[2][2], const T Ai[2][2],
             Prr[i][j] = sg * (c * pr_);
             Pri[i][j] = sg * (c * pi_);
         }
+    if (sine) {
+        /* Eq. 31: each element of P_r* U is d_ii z_ij (Eq. 5), the (2,1)
+         * element negated, with z from the sines and cosines (sin = cos tan,
+         * Sec. 7) and d^_22 = dhr + i dhi:
+         * z11 = pp - d^ qq, z12 = rr + d^ tt, z21 = tt + d^ rr, z22 = d^ pp - qq,
+         * pp = cos a cos p, qq = sin a sin p, rr = cos a sin p, tt = sin a cos p. */
+        const T sina = cosa * tana, sinp = cosp * tanp;
+        const T pp = cosa * cosp, qq = sina * sinp, rr = cosa * sinp, tt = sina * cosp;
+        T zr[2][2], zi[2][2];
+        zr[0][0] = T_FMA(-dhr, qq, pp);   zi[0][0] = -(dhi * qq);
+        zr[0][1] = T_FMA(dhr, tt, rr);    zi[0][1] = dhi * tt;
+        zr[1][0] = T_FMA(dhr, rr, tt);    zi[1][0] = dhi * rr;
+        zr[1][1] = T_FMA(dhr, pp, -qq);   zi[1][1] = dhi * pp;
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                const T pr_ = T_FMA(dr[i], zr[i][j], -(di[i] * zi[i][j]));
+                const T pi_ = T_FMA(dr[i], zi[i][j], di[i] * zr[i][j]);
+                const T sg = (i == 1 && j == 0) ? (T)-1 : (T)1;
+                Prr[i][j] = sg * pr_;
+                Pri[i][j] = sg * pi_;
+            }
+    }
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
             Ur[i][j] = Prr[pr ? 1 - i : i][j];

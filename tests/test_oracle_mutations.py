@@ -27,6 +27,15 @@ MUTATIONS = {
                               "T_WIDE_FMA(-mtw, (T_WIDE)A3[1][1], (T_WIDE)A3[0][1]);"),
     "wide_test_reversed": ("if (T_FABS(r22pp) < tau * r11) {", "if (T_FABS(r22pp) > tau * r11) {"),
     "wide_cos_dropped": ("r22pp = cosa * (T)g;", "r22pp = (T)g;"),
+    # the sine-based assembly of Eq. 31
+    "eq31_dhat_sign": ("zr[0][0] = T_FMA(-dhr, qq, pp);", "zr[0][0] = T_FMA(dhr, qq, pp);"),
+    "eq31_terms_swapped": ("zr[0][1] = T_FMA(dhr, tt, rr);", "zr[0][1] = T_FMA(dhr, rr, tt);"),
+    "eq31_real_u21_sign": ("Ur[1][0] = -(d[1] * T_FMA(dh, rr, tt));",
+                           "Ur[1][0] = (d[1] * T_FMA(dh, rr, tt));"),
+    "eq31_sine_without_cos": ("const T sina = cosa * tana, sinp = cosp * tanp;",
+                              "const T sina = tana, sinp = cosp * tanp;"),
+    "eq31_d22_conj": ("const T pi_ = T_FMA(dr[i], zi[i][j], di[i] * zr[i][j]);",
+                      "const T pi_ = T_FMA(dr[i], zi[i][j], -(di[i] * zr[i][j]));"),
     "u21_sign": ("Ur[1][0] = -(c * (d[1] * T_FMA(dh, tanp, tana)));",
                  "Ur[1][0] = (c * (d[1] * T_FMA(dh, tanp, tana)));"),
     "tanpsi_transposed": ("const T tanq = T_FMA(y, tanp, -x);",
@@ -93,6 +102,17 @@ def pin_failures(o):
         if not (np.nanmax(ex) <= 8 and sel.any() and np.nanmax(en[sel]) <= 8
                 and np.all(w[ratio < 2.0**-5 * 0.999]) and not np.any(w & (ratio > 2.0**-4 * 1.001))):
             failed.append("tan64")
+        # the sine-based assembly of Eq. 31: accuracy of Sec. 8 and agreement
+        # with the tangent form
+        for rows, seed in ((4, 904), (8, 905)):
+            A = inputs.normal_batch(3000, rows, seed)
+            t = o.svd2(A)
+            r = o.svd2(A, sine=True)
+            m = o.metrics(A, r["U"], r["V"], r["smax"], r["smin"], r["s"])
+            if not (m["rho"].max() <= 8 * EPS64
+                    and max(m["delta"].max(), m["eta"].max()) <= 16 * EPS64
+                    and np.abs(r["U"] - t["U"]).max() <= 3 * EPS64):
+                failed.append(f"eq31_{rows}")
         for row in read_rows("hand_cases.txt"):
             fields = dict(tok.split("=") for tok in row[1:])
             A = np.array([[hexf(t)] for t in fields["A"].split(",")])

@@ -571,3 +571,46 @@ def test_tan64_threshold_zero_and_extremes():
     zero = np.all(A == 0, axis=0)
     assert not r1["wide"][zero].any()
     assert r1["count"] > 0.9 * A.shape[1]
+
+
+# ------------------------------------------- the sine-based assembly of Eq. 31
+
+@pytest.mark.parametrize("rows,dt", [(4, np.float64), (8, np.float64), (4, np.float32),
+                                     (8, np.float32)])
+def test_sine_assembly_eq31(rows, dt):
+    """U assembled by Eq. 31 from sin = cos tan (Sec. 7) instead of the tangent
+    form of Eq. 29: the two are the same matrix in exact arithmetic, V and the
+    singular values are unchanged, and the decomposition keeps the accuracy
+    the paper measures (Sec. 8): rho <= 8 eps, delta and eta <= 16 eps; the
+    rounding of the two forms differs by a few eps per entry."""
+    eps = 2.0**-52 if dt == np.float64 else 2.0**-23
+    A = inputs.normal_batch(30000, rows, 41, dt)
+    if dt == np.float64:
+        A = np.concatenate([A, inputs.random_bits(2000, rows, 42)], axis=1)
+    t = oracle.svd2(A)
+    s = oracle.svd2(A, sine=True)
+    for k in ("V", "smax", "smin"):
+        assert bits_equal(t[k], s[k]), k
+    assert np.array_equal(t["s"], s["s"]) and np.array_equal(t["piv"], s["piv"])
+    assert np.abs(t["U"].astype(np.float64) - s["U"].astype(np.float64)).max() <= 3 * eps
+    d = lambda x: x.astype(np.float64)
+    m = oracle.metrics(d(A), d(s["U"]), d(s["V"]), d(s["smax"]), d(s["smin"]), s["s"])
+    assert m["rho"].max() <= 8 * eps
+    assert max(m["delta"].max(), m["eta"].max()) <= 16 * eps
+
+
+def test_sine_assembly_exact_cases():
+    """Diagonal and zero matrices: alpha = phi = 0 makes every sine a signed
+    zero and every cosine 1, so both assemblies are exact and agree bit for
+    bit, signed zeros included; the golden hand cases hold for Eq. 31 too."""
+    A = np.array([[2.0, 0.0, 0.0, -3.0], [0.0, 0.0, 0.0, 0.0], [-5.0, 0.0, 0.0, 0.5],
+                  [0.0, 0.0, 0.0, 7.0]]).T.copy()
+    t = oracle.svd2(A)
+    s = oracle.svd2(A, sine=True)
+    assert bits_equal(t["U"], s["U"]) and bits_equal(t["V"], s["V"])
+    for row in read_rows("hand_cases.txt"):
+        fields = dict(tok.split("=") for tok in row[1:])
+        A1 = np.array([[hexf(tok)] for tok in fields["A"].split(",")])
+        r = oracle.svd2(A1, sine=True)
+        U = np.array([hexf(tok) for tok in fields["U"].split(",")])
+        assert bits_equal(r["U"][:, 0], U), row[0]
