@@ -4,12 +4,17 @@
 A step is one pass of the whole hot path -- scaling (Eq. 2), URV (Eq. 4 -
 Eq. 11), SVD of R (Eq. 13 - Eq. 17), assembly of U and V (Eq. 29) and the
 stores -- over one batch of synthetic input.  The default workload is the
-complex128 batch of n = 2^24 matrices (real and imaginary parts uniform in
-[-1, 1] times 2^e, e uniform in [-500, 500] per matrix, 1% rank-deficient),
-generated by the seeded generator in ``paper_2005_07403_gb300.inputs`` and
-resident in HBM before the timed region.  Its 1 GiB of input (3.3 GiB moved
-per step) is far larger than the 129 MB L2, so no flush is needed between
-steps.
+FP32-vs-FP64 batch of n = 2^26 real matrices (90% i.i.d. N(0,1) entries, 10%
+R(t1) diag(1, 10^-u) R(t2)^T with u uniform in [2, 12], generated in FP64 and
+rounded to FP32) in the FP32 form that takes the tangent step of Eq. 6 - Eq. 7
+in FP64 where the matrix is ill-conditioned, generated by the seeded generator
+in ``paper_2005_07403_gb300.inputs`` and resident in HBM before the timed
+region.  Its 1 GiB of input (4 GiB moved per step) is far larger than the
+129 MB L2, so no flush is needed between steps.  The line also carries the
+comparison with the FP64 form on the same inputs (matrices/s and the FP32
+forms' singular-value errors against it); the supplementary measurements
+(threshold sweeps, complex128, batching, differentiation, layouts,
+Kogbetliantz step) go to stderr as one JSON object, or to ``--report FILE``.
 
 Multi-GPU (torchrun): every rank processes its own batch of the same size
 (independent problems, weak scaling); there is no data-path collective, only a
@@ -50,9 +55,22 @@ WORKLOADS = {
                       desc="real FP64 n=2^26 (FP32-vs-FP64 batch widened exactly)"),
     "real-fp32": dict(rows=4, n=2**26, bytes_per=16 + 32 + 8 + 4, kind="s", form="plain",
                       dtype="f32", desc="real FP32 n=2^26 (FP32-vs-FP64 batch), no re-run"),
+    "real-fp32-tan64": dict(rows=4, n=2**26, bytes_per=16 + 32 + 8 + 4, kind="s", form="tan64",
+                            dtype="f32",
+                            desc="real FP32 n=2^26 (90% N(0,1), 10% R(t1) diag(1, 10^-u) R(t2)^T, "
+                                 "u in [2,12]), FP64 tangent step (Eq. 6 - Eq. 7) where "
+                                 "|r''22| < 2^-3 r11"),
     "real-fp32-rerun": dict(rows=4, n=2**26, bytes_per=16 + 32 + 8 + 4, kind="s", form="rerun",
                             dtype="f32",
                             desc="real FP32 n=2^26 with FP64 re-run below tau = 2^-8"),
+    # forward (with back-scaling) plus the adjoint: fwd 116 / 60 B, adjoint 192 / 96 B
+    "grad-fp64": dict(rows=4, n=2**22, bytes_per=116 + 192, kind="d", form="grad", dtype="f64",
+                      desc="real FP64 n=2^22 forward + adjoint: A = R(t1) diag(s1, s2) R(t2)^T, "
+                           "s1 ~ U[0.5, 2], relative gap log-uniform in [1e-3, 1] (90%) and "
+                           "[1e-12, 1e-6] (10%), upstream gradients N(0,1)"),
+    "grad-fp32": dict(rows=4, n=2**22, bytes_per=60 + 96, kind="s", form="grad", dtype="f32",
+                      desc="real FP32 n=2^22 forward + adjoint (the FP64 workload rounded "
+                           "to FP32)"),
     "complex64": dict(rows=8, n=2**25, bytes_per=32 + 64 + 8 + 4, kind="c", form="plain",
                       dtype="f32",
                       desc="complex FP32 n=2^25 (90% N(0,1), 10% ill-conditioned), no re-run"),
@@ -64,7 +82,13 @@ WORKLOADS = {
 
 
 def make_input(name, n, rank):
+    """The workload's A; for the differentiation workloads a dict with A and the
+    upstream gradients gU, gV, gS."""
     from paper_2005_07403_gb300 import inputs
+    if name.startswith("grad-"):
+        g = inputs.grad_batch(n, seed=inputs.SEED_CFG5 + rank)
+        dt = np.float64 if name == "grad-fp64" else np.float32
+        return {k: np.ascontiguousarray(g[k].astype(dt)) for k in ("A", "gU", "gV", "gS")}
     if name == "complex128":
         return inputs.complex_scaled(n, seed=inputs.SEED_CFG2 + rank)
     if name in ("complex64", "complex64-rerun"):
@@ -73,13 +97,19 @@ def make_input(name, n, rank):
     return A32.astype(np.float64) if name == "real-fp64" else A32
 
 
+# threshold of the FP32 forms (log2): the tangent step's default and the re-run's
+TAN64_TAU_LOG2 = -3
+RERUN_TAU_LOG2 = -8
+DEFAULT_WORKLOAD = "real-fp32-tan64"
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="complex128")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n", type=int, default=0,
@@ -87,7 +117,9 @@ def parse():
     p.add_argument("--no-tune", action="store_true",
                    help="keep the library's default launch shape")
     p.add_argument("--no-compare", action="store_true",
-                   help="skip the FP32-vs-FP64 comparison block")
+                   help="skip the FP32-vs-FP64 comparison and the supplementary report")
+    p.add_argument("--report", default="",
+                   help="write the supplementary report (JSON) to this file instead of stderr")
     return p.parse_args()
 
 
@@ -134,6 +166,8 @@ FP64_OPS_VALUES_Z = 89 - 38
 # also covers the shared headers, the C header and the build script.
 KERNEL_SOURCES = {"complex128": "svd2_fwd_z.cu", "real-fp64": "svd2_fwd_d.cu",
                   "real-fp32": "svd2_fwd_s.cu", "real-fp32-rerun": "svd2_rerun.cu",
+                  "real-fp32-tan64": "svd2_tan64.cu", "grad-fp64": "svd2_bwd.cu",
+                  "grad-fp32": "svd2_bwd.cu",
                   "complex64": "svd2_fwd_c.cu", "complex64-rerun": "svd2_rerun.cu"}
 
 
@@ -245,41 +279,62 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(A, rows, min_seconds=10.0, sample=2**21):
-    """The oracle as it stands, on all host cores, over a bounded sample of the
-    workload (the first `sample` matrices), repeated for at least min_seconds."""
+def oracle_form(W, cores):
+    """The oracle's counterpart of the workload's form, as a function of one
+    (rows, n) host batch (a dict of A and the gradients for "grad")."""
     import oracle
+    if W["form"] == "grad":
+        def fwd_bwd(g):
+            r = oracle.svd2(g["A"], backscale=True, nthreads=cores)
+            dl = 64 * float(np.finfo(g["A"].dtype).eps)
+            return oracle.bwd(r["U"], r["V"], r["smax"], r["smin"], g["gU"], g["gV"],
+                              g["gS"][0], g["gS"][1], dl)
+        return fwd_bwd
+    if W["form"] == "rerun":
+        return lambda a: oracle.svd2_rerun(a, RERUN_TAU_LOG2, nthreads=cores)
+    if W["form"] == "tan64":
+        return lambda a: oracle.svd2_tan64(a, TAN64_TAU_LOG2, nthreads=cores)
+    return lambda a: oracle.svd2(a, nthreads=cores)
+
+
+def _head(A, m):
+    """The first m matrices of a workload's input (an array, or the dict of the
+    differentiation workloads)."""
+    if isinstance(A, dict):
+        return {k: np.ascontiguousarray(v[..., :m]) for k, v in A.items()}
+    return np.ascontiguousarray(A[:, :m])
+
+
+def cpu_baseline(A, W, min_seconds=10.0, sample=2**21):
+    """The oracle as it stands, in the workload's form, on all host cores, over a
+    bounded sample of the workload (the first `sample` matrices), repeated for
+    at least min_seconds."""
     cores = host_cores()
-    S = np.ascontiguousarray(A[:, :sample])
-    oracle.svd2(S[:, :1024], nthreads=cores)          # build/load outside the timing
+    run = oracle_form(W, cores)
+    S = _head(A, sample)
+    run(_head(S, 1024))                              # build/load outside the timing
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.svd2(S, nthreads=cores)
+        run(S)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
             break
     return {"value": reps * S.shape[1] / el, "unit": "matrices/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"first {S.shape[1]} matrices of the workload, {reps} passes, {el:.1f} s"}
+            "sample": f"first {sample} matrices of the workload, {reps} passes, {el:.1f} s"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
     cores = host_cores()
     W = WORKLOADS[args.workload]
     sample = 2**21
     A = make_input(args.workload, sample, 0)
-    if W["form"] == "rerun":
-        def run(a):
-            return oracle.svd2_rerun(a, -8, nthreads=cores)
-    else:
-        def run(a):
-            return oracle.svd2(a, nthreads=cores)
-    run(np.ascontiguousarray(A[:, :1024]))
+    run = oracle_form(W, cores)
+    run(_head(A, 1024))
     for _ in range(args.warmup):
         run(A)
     t0 = time.perf_counter()
@@ -300,9 +355,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _caller(S, W, Ad, out, workspace):
+def _caller(S, W, Ad, out, workspace, G=None):
+    if W["form"] == "grad":
+        import torch
+        gA = torch.empty_like(Ad)
+        dl = S.default_rel_delta(Ad.dtype)
+
+        def step():
+            S.svd2(Ad, backscale=True, out=out)
+            S.svd2_bwd(out.U, out.V, out.smax, out.smin, G["gU"], G["gV"], G["gS"][0],
+                       G["gS"][1], dl, out=gA)
+        return step
     if W["form"] == "rerun":
-        return lambda: S.svd2_rerun(Ad, out=out, workspace=workspace)
+        return lambda: S.svd2_rerun(Ad, tau_log2=RERUN_TAU_LOG2, out=out, workspace=workspace)
+    if W["form"] == "tan64":
+        return lambda: S.svd2_tan64(Ad, tau_log2=TAN64_TAU_LOG2, out=out)
     return lambda: S.svd2(Ad, out=out)
 
 
@@ -360,71 +427,115 @@ def error_metrics(torch, A, r):
     return out
 
 
-def compare_fp32_fp64(torch, S, steps, warmup, stream, n=2**26):
-    """FP32 form (with FP64 re-run) against the FP64 form on the same inputs:
-    matrices/s of each and the FP32 form's error against the FP64 form (which
-    reproduces the FP64 method bit for bit), on the whole batch."""
-    from paper_2005_07403_gb300 import inputs
-    A32, _ = inputs.real_fp32_illcond(n)
+def compare_precisions(torch, S, steps, warmup, stream, n=2**26):
+    """The FP32 forms against the FP64 form on the same inputs (the FP32-vs-FP64
+    batch of n = 2^26: 90% N(0,1), 10% ill-conditioned with sigma ratio 10^-u,
+    u in [2, 12], rounded to FP32; the FP64 form runs on the exact widening).
+    Each form's matrices/s, and its singular values' error against the FP64
+    form (which reproduces the double method bit for bit) in units of
+    u = 2^-24: max and 99th percentile, sigma'_min separately for the
+    well- and the ill-conditioned class.  Returns (summary, report): a flat
+    dict of scalars for the bench line and the detailed report with the
+    threshold sweeps of the two forms that use double precision."""
+    from paper_2005_07403_gb300 import inputs, tune
+    A32, ill = inputs.real_fp32_illcond(n)
     A32d = torch.from_numpy(A32).cuda()
     A64d = A32d.double()
+    illd = torch.from_numpy(ill).cuda()
     del A32
     o64 = S.empty_result(4, n, torch.float64, A64d.device)
     o32 = S.empty_result(4, n, torch.float32, A32d.device)
     ws = S.rerun_workspace(n)
-    from paper_2005_07403_gb300 import tune
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     shapes = {"fp64": tune.tune(A64d, o64, reps=3), "fp32": tune.tune(A32d, o32, reps=3)}
-    ms64 = time_steps(torch, lambda: S.svd2(A64d, out=o64), steps, warmup, stream)
-    ms32r = time_steps(torch, lambda: S.svd2_rerun(A32d, out=o32, workspace=ws), steps, warmup,
-                       stream)
-    rerun = S.rerun_count(ws)
-    ms32 = time_steps(torch, lambda: S.svd2(A32d, out=o32), steps, warmup, stream)
-    torch.cuda.synchronize()
     u = 2.0**-24
+    ms = {"fp64": time_steps(torch, lambda: S.svd2(A64d, out=o64), steps, warmup, stream)}
+    torch.cuda.synchronize()
     sx64 = torch.ldexp(o64.smax, -o64.s.double())
     sn64 = torch.ldexp(o64.smin, -o64.s.double())
-    nz = o64.smax > 0
-    q = lambda x: _quantile(torch, x, 0.99)
+    nz = (o64.smax > 0) & (sn64 > 0)
+    q99 = lambda x: _quantile(torch, x, 0.99) if x.numel() else 0.0
 
-    def sigma_errors(o):
-        sx32 = torch.ldexp(o.smax.double(), -o.s.double())
-        sn32 = torch.ldexp(o.smin.double(), -o.s.double())
-        ex = ((sx32 - sx64).abs() / sx64)[nz]
-        en = ((sn32 - sn64).abs() / sn64)
-        return ex, en
+    def errors(o):
+        sx = torch.ldexp(o.smax.double(), -o.s.double())
+        sn = torch.ldexp(o.smin.double(), -o.s.double())
+        ex = ((sx - sx64).abs() / sx64)[o64.smax > 0] / u
+        en = ((sn - sn64).abs() / torch.where(nz, sn64, torch.ones_like(sn64))) / u
+        ew, ei = en[nz & ~illd], en[nz & illd]
+        return {"smax_max": float(ex.max()), "smax_p99": q99(ex),
+                "smin_max_normal": float(ew.max()), "smin_p99_normal": q99(ew),
+                "smin_max_illcond": float(ei.max()), "smin_p99_illcond": q99(ei)}
 
-    # the plain FP32 form (o32 holds its results), then the re-run form
-    ex, en = sigma_errors(o32)
-    plain_err = {"smax_max": float(ex.max() / u), "smax_p99": q(ex) / u,
-                 "smin_max": float(en[nz & (sn64 > 0)].max() / u),
-                 "smin_p99": q(en[nz & (sn64 > 0)]) / u}
-    metrics = {"fp64": error_metrics(torch, A64d, o64),
-               "fp32_plain": error_metrics(torch, A32d, o32)}
-    S.svd2_rerun(A32d, out=o32, workspace=ws)
-    torch.cuda.synchronize()
-    ex, en = sigma_errors(o32)
-    keep = (o32.smin >= 2.0**S.RERUN_TAU_LOG2 * o32.smax) & nz & (sn64 > 0)
-    redo = ~keep & nz & (sn64 > 0)
-    metrics["fp32_rerun"] = error_metrics(torch, A32d, o32)
-    metrics["kappa_max"] = float((sx64 / sn64)[nz].max())
+    forms = {
+        "fp32_plain": lambda: S.svd2(A32d, out=o32),
+        "fp32_tan64": lambda: S.svd2_tan64(A32d, tau_log2=TAN64_TAU_LOG2, out=o32),
+        "fp32_rerun": lambda: S.svd2_rerun(A32d, tau_log2=RERUN_TAU_LOG2, out=o32, workspace=ws),
+    }
+    err, metrics = {}, {"fp64": error_metrics(torch, A64d, o64)}
+    frac = {}
+    for name, f in forms.items():
+        ms[name] = time_steps(torch, f, steps, warmup, stream)
+        cnt.zero_()
+        if name == "fp32_tan64":
+            S.svd2_tan64(A32d, tau_log2=TAN64_TAU_LOG2, out=o32, count=cnt)
+        else:
+            f()
+        torch.cuda.synchronize()
+        if name == "fp32_tan64":
+            frac[name] = int(cnt.item()) / n
+        elif name == "fp32_rerun":
+            frac[name] = S.rerun_count(ws) / n
+        err[name] = errors(o32)
+        metrics[name] = error_metrics(torch, A32d, o32)
+    # the threshold sweeps: throughput, share of matrices in double, sigma errors
+    sweep = {"fp32_tan64": [], "fp32_rerun": []}
+    for t in (-1, -2, -3, -4, -6, -8, -10, -12):
+        f = lambda: S.svd2_tan64(A32d, tau_log2=t, out=o32)
+        m = time_steps(torch, f, 5, 3, stream)
+        cnt.zero_()
+        S.svd2_tan64(A32d, tau_log2=t, out=o32, count=cnt)
+        torch.cuda.synchronize()
+        sweep["fp32_tan64"].append(dict(tau_log2=t, matrices_per_s=n / (m / 1e3),
+                                        double_fraction=int(cnt.item()) / n, **errors(o32)))
+    for t in (-4, -8, -12):
+        f = lambda: S.svd2_rerun(A32d, tau_log2=t, out=o32, workspace=ws)
+        m = time_steps(torch, f, 5, 3, stream)
+        f()
+        torch.cuda.synchronize()
+        sweep["fp32_rerun"].append(dict(tau_log2=t, matrices_per_s=n / (m / 1e3),
+                                        double_fraction=S.rerun_count(ws) / n, **errors(o32)))
+    peak, _ = measured_peaks()
+    fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3
+    rate = {k: n / (v / 1e3) for k, v in ms.items()}
+    summary = {
+        "n": n, "u": "2^-24",
+        "fp64_matrices_per_s": rate["fp64"],
+        "fp64_fp64_pipe_frac": FP64_OPS_PER_MATRIX["d"] * rate["fp64"] / 1e9 / fp64_peak,
+        "fp32_plain_matrices_per_s": rate["fp32_plain"],
+        "fp32_plain_hbm_frac": 60 * rate["fp32_plain"] / 1e9 / peak,
+        "fp32_tan64_matrices_per_s": rate["fp32_tan64"],
+        "fp32_tan64_hbm_frac": 60 * rate["fp32_tan64"] / 1e9 / peak,
+        "fp32_tan64_tau_log2": TAN64_TAU_LOG2,
+        "fp32_tan64_double_fraction": frac["fp32_tan64"],
+        "fp32_rerun_matrices_per_s": rate["fp32_rerun"],
+        "fp32_rerun_tau_log2": RERUN_TAU_LOG2,
+        "fp32_rerun_double_fraction": frac["fp32_rerun"],
+    }
+    for name in forms:
+        e = err[name]
+        summary[name + "_smax_err_max_u"] = e["smax_max"]
+        summary[name + "_smin_err_max_u"] = max(e["smin_max_normal"], e["smin_max_illcond"])
+        summary[name + "_smin_err_p99_illcond_u"] = e["smin_p99_illcond"]
+        summary[name + "_rho_max"] = metrics[name]["rho_max"]
+    summary["fp64_rho_max"] = metrics["fp64"]["rho_max"]
     metrics["evaluated_in"] = ("FP64 on the exact widening of each form's outputs (Eq. 32 - "
                                "Eq. 35); the FP64 form's values are at the level of that "
                                "evaluation's own rounding")
-    out = {"n": n, "tau_log2": S.RERUN_TAU_LOG2, "tuned_shapes": shapes,
-           "fp64": {"matrices_per_s": n / (ms64 / 1e3), "ms": ms64},
-           "fp32_rerun": {"matrices_per_s": n / (ms32r / 1e3), "ms": ms32r,
-                          "rerun_fraction": rerun / n},
-           "fp32_plain": {"matrices_per_s": n / (ms32 / 1e3), "ms": ms32},
-           "fp32_plain_error_vs_fp64_u": plain_err,
-           "fp32_rerun_error_vs_fp64_u": {
-               "smax_max": float(ex.max() / u), "smax_p99": q(ex) / u,
-               "smin_max_kept": float(en[keep].max() / u), "smin_p99_kept": q(en[keep]) / u,
-               "smin_max_rerun": float(en[redo].max() / u), "smin_p99_rerun": q(en[redo]) / u,
-               "u": "2^-24"},
-           "error_metrics": metrics}
-    del A32d, A64d, o64, o32, ws
+    report = {"n": n, "tuned_shapes": shapes, "ms": ms, "errors_vs_fp64_u": err,
+              "error_metrics": metrics, "tau_sweep": sweep}
+    del A32d, A64d, o64, o32, ws, illd
     torch.cuda.empty_cache()
-    return out
+    return summary, report
 
 
 def bench_multi(torch, S, stream, replays=20):
@@ -463,50 +574,79 @@ def bench_multi(torch, S, stream, replays=20):
     return out
 
 
+# The adjoint kernels' algorithmic traffic per matrix: U, V, s1, s2, gU, gV,
+# g1, g2 read and gA written once (real: 20 + 4 values, complex: 36 + 8), and
+# the real FP64 adjoint's FP64 add/mul per matrix counted from its formulas
+# (J and K 12, a and b 2, s1 + s2 1, the gap 5, p and q 6, M 2, U M 12,
+# (U M) V^T 12; its three divisions run on the integer pipe).
+BWD_BYTES = {"fp64": 24 * 8, "fp32": 24 * 4, "complex128": 44 * 8, "complex64": 44 * 4}
+BWD_FP64_OPS_REAL = 52
+
+
 def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
     """The differentiation workload: A = R(t1) diag(s1, s2) R(t2)^T, 10% with
-    relative gaps in [1e-12, 1e-6], N(0,1) upstream gradients; one step is the
-    forward kernel (with back-scaling) plus the adjoint kernel, FP64 and FP32."""
+    relative gaps in [1e-12, 1e-6], N(0,1) upstream gradients (complex: N(0,1)
+    parts drawn on the device).  Per dtype: the forward kernel (with
+    back-scaling) and the adjoint kernel timed each on its own with CUDA
+    events, their sum as the step, and the adjoint's roofline: HBM bytes for
+    every form, FP64-pipe operations for real FP64."""
     from paper_2005_07403_gb300 import inputs
+    peak, _ = measured_peaks()
+    fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3
     g = inputs.grad_batch(n)
     out = {"n": n}
+    cases = []
     for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
-        A = torch.from_numpy(g["A"]).to("cuda", dt)
-        gU = torch.from_numpy(g["gU"]).to("cuda", dt)
-        gV = torch.from_numpy(g["gV"]).to("cuda", dt)
-        gS = torch.from_numpy(g["gS"]).to("cuda", dt)
-        r = S.empty_result(4, n, dt, A.device)
-        gA = torch.empty_like(A)
-
-        def step():
-            S.svd2(A, backscale=True, out=r)
-            S.svd2_bwd(r.U, r.V, r.smax, r.smin, gU, gV, gS[0], gS[1], out=gA)
-
-        ms = time_steps(torch, step, steps, warmup, stream)
-        msf = time_steps(torch, lambda: S.svd2(A, backscale=True, out=r), steps, warmup, stream)
-        out[name] = {"fwd_bwd_matrices_per_s": n / (ms / 1e3), "fwd_bwd_ms": ms,
-                     "bwd_ms": ms - msf}
-        del A, gU, gV, gS, r, gA
-    # complex: N(0,1) parts and upstream gradients drawn on the device
+        cases.append((name, 4, lambda dt=dt: (torch.from_numpy(g["A"]).to("cuda", dt),
+                                               torch.from_numpy(g["gU"]).to("cuda", dt),
+                                               torch.from_numpy(g["gV"]).to("cuda", dt),
+                                               torch.from_numpy(g["gS"]).to("cuda", dt))))
     for name, dt in (("complex128", torch.float64), ("complex64", torch.float32)):
-        A = inputs.normal_batch_device(n, 8, 151, "cuda", dt)
-        gU = inputs.normal_batch_device(n, 8, 152, "cuda", dt)
-        gV = inputs.normal_batch_device(n, 8, 153, "cuda", dt)
-        gS = inputs.normal_batch_device(n, 2, 154, "cuda", dt)
-        r = S.empty_result(8, n, dt, A.device)
+        cases.append((name, 8, lambda dt=dt: (inputs.normal_batch_device(n, 8, 151, "cuda", dt),
+                                               inputs.normal_batch_device(n, 8, 152, "cuda", dt),
+                                               inputs.normal_batch_device(n, 8, 153, "cuda", dt),
+                                               inputs.normal_batch_device(n, 2, 154, "cuda", dt))))
+    for name, rows, make in cases:
+        A, gU, gV, gS = make()
+        r = S.empty_result(rows, n, A.dtype, A.device)
         gA = torch.empty_like(A)
-
-        def step():
-            S.svd2(A, backscale=True, out=r)
-            S.svd2_bwd(r.U, r.V, r.smax, r.smin, gU, gV, gS[0], gS[1], out=gA)
-
-        ms = time_steps(torch, step, steps, warmup, stream)
-        msf = time_steps(torch, lambda: S.svd2(A, backscale=True, out=r), steps, warmup, stream)
-        out[name] = {"fwd_bwd_matrices_per_s": n / (ms / 1e3), "fwd_bwd_ms": ms,
-                     "bwd_ms": ms - msf}
+        fwd = lambda: S.svd2(A, backscale=True, out=r)
+        bwd = lambda: S.svd2_bwd(r.U, r.V, r.smax, r.smin, gU, gV, gS[0], gS[1], out=gA)
+        msf = time_steps(torch, fwd, steps, warmup, stream)
+        fwd()
+        msb = time_steps(torch, bwd, steps, warmup, stream)
+        res = {"fwd_ms": msf, "bwd_ms": msb, "fwd_bwd_matrices_per_s": n / ((msf + msb) / 1e3),
+               "bwd_matrices_per_s": n / (msb / 1e3), "bwd_bytes_per_matrix": BWD_BYTES[name],
+               "bwd_hbm_frac": BWD_BYTES[name] * n / (msb / 1e3) / 1e9 / peak}
+        if name == "fp64":
+            res["bwd_fp64_ops_per_matrix"] = BWD_FP64_OPS_REAL
+            res["bwd_fp64_pipe_frac"] = BWD_FP64_OPS_REAL * n / (msb / 1e3) / 1e9 / fp64_peak
+        out[name] = res
         del A, gU, gV, gS, r, gA
     torch.cuda.empty_cache()
     return out
+
+
+def bench_complex128(torch, S, stream, steps=10, warmup=3):
+    """The complex128 workload (n = 2^24, parts U[-1,1] 2^e, e in [-500, 500]
+    per matrix, 1% rank-deficient) on the plain FP64 form: matrices/s, the
+    fraction of the FP64 pipe (89 add/mul/fma per matrix) and of HBM (212 B)."""
+    from paper_2005_07403_gb300 import tune
+    W = WORKLOADS["complex128"]
+    n = W["n"]
+    Ad = torch.from_numpy(make_input("complex128", n, 0)).cuda()
+    out = S.empty_result(8, n, Ad.dtype, Ad.device)
+    shape = tune.tune(Ad, out, reps=3)
+    ms = time_steps(torch, lambda: S.svd2(Ad, out=out), steps, warmup, stream)
+    peak, _ = measured_peaks()
+    fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3
+    rate = n / (ms / 1e3)
+    res = {"n": n, "ms": ms, "matrices_per_s": rate, "tuned_shape": shape,
+           "fp64_pipe_frac": FP64_OPS_PER_MATRIX["z"] * rate / 1e9 / fp64_peak,
+           "hbm_frac": W["bytes_per"] * rate / 1e9 / peak}
+    del Ad, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_variants(torch, S, stream, steps=10, warmup=3):
@@ -600,15 +740,21 @@ def run_ours(args):
     W = WORKLOADS[args.workload]
     n = args.n or W["n"]
     A = make_input(args.workload, n, rank)
-    Ad = torch.from_numpy(A).cuda()
+    G = None
+    if W["form"] == "grad":
+        G = {k: torch.from_numpy(v).cuda() for k, v in A.items()}
+        Ad = G["A"]
+    else:
+        Ad = torch.from_numpy(A).cuda()
     out = S.empty_result(W["rows"], n, Ad.dtype, Ad.device)
     workspace = S.rerun_workspace(n) if W["form"] == "rerun" else None
-    call = _caller(S, W, Ad, out, workspace)
+    call = _caller(S, W, Ad, out, workspace, G)
     S.lib()
     tuned = None
     if not args.no_tune:
         from paper_2005_07403_gb300 import tune
-        tuned = tune.tune(Ad, out, reps=3)   # launch shape from the autotuner (cached)
+        # launch shape from the autotuner (cached)
+        tuned = tune.tune(Ad, out, reps=3, form="tan64" if W["form"] == "tan64" else "plain")
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -641,23 +787,24 @@ def run_ours(args):
     # our kernels per call: the batch kernel and its fix-up pass (plus a memset
     # of the flag word); the re-run form also the list compaction and the
     # re-run pass
-    launches_per_step = 4 if W["form"] == "rerun" else 2
+    launches_per_step = {"rerun": 4, "grad": 3}.get(W["form"], 2)
 
     # end to end through the C ABI with host buffers (svd2_batch_host): every
-    # step copies A in and every output out through the chunked pipeline
+    # step reads A from and writes every output to pinned host memory
     e2e = None
-    if not args.no_e2e and W["form"] == "plain":
+    if not args.no_e2e and W["form"] in ("plain", "tan64"):
+        t64 = W["form"] == "tan64"
         Ah = torch.from_numpy(A).pin_memory()
         outs_h = S.empty_host_result(W["rows"], n, Ah.dtype)
         h2d = Ah.numel() * Ah.element_size()
         d2h = sum(t.numel() * t.element_size()
                   for t in (outs_h.U, outs_h.V, outs_h.smax, outs_h.smin, outs_h.s))
         ke = max(2, min(args.steps, 5))
-        S.svd2_host(Ah, out=outs_h)        # warm-up: creates the staging buffers
+        S.svd2_host(Ah, out=outs_h, tan64=t64)        # warm-up: creates the staging buffers
         barrier()
         e0.record(stream)
         for _ in range(ke):
-            S.svd2_host(Ah, out=outs_h)
+            S.svd2_host(Ah, out=outs_h, tan64=t64)
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1)
@@ -681,7 +828,7 @@ def run_ours(args):
            "note": f"peak {peak_src}; algorithmic {W['bytes_per']} B/matrix x {n} per launch"
                    + ("; traffic from profiles/dram_traffic.txt scaled to n" if traffic else "")}
     if W["kind"] in FP64_OPS_PER_MATRIX:
-        ops = FP64_OPS_PER_MATRIX[W["kind"]]
+        ops = FP64_OPS_PER_MATRIX[W["kind"]] + (BWD_FP64_OPS_REAL if W["form"] == "grad" else 0)
         fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3   # G op/s
         fp64_achieved = ops * n / (ms_per_step / 1e3) / 1e9
         roofline = {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak,
@@ -699,25 +846,50 @@ def run_ours(args):
             "dtype": W["dtype"], "data": "synthetic",
             "config": {"workload": W["desc"], "n_per_gpu": n,
                        "l2": "inputs larger than L2 (>= 1 GiB per step)",
-                       "launch": S.get_launch(W["kind"]),
+                       "launch": "block %d, mpt %d, unroll %d, waves %d" % S.get_launch(
+                           "s_tan64" if W["form"] == "tan64" else W["kind"]),
                        "launch_from": "autotuner" if tuned else "default"},
             "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk}
-    if rank == 0 and world == 1 and not args.no_compare and args.workload == "complex128" \
+    if W["form"] == "tan64":
+        line["config"]["tau_log2"] = TAN64_TAU_LOG2
+    report = None
+    if rank == 0 and world == 1 and not args.no_compare and args.workload == DEFAULT_WORKLOAD \
             and not args.n:
         del Ad, out
         torch.cuda.empty_cache()
-        line["fp32_vs_fp64"] = compare_fp32_fp64(torch, S, max(3, min(args.steps, 10)),
-                                                 args.warmup, stream)
-        line["multi_batch"] = bench_multi(torch, S, stream)
-        line["differentiation"] = bench_grad(torch, S, stream)
-        line["variants"] = bench_variants(torch, S, stream)
-        line["kogbetliantz_step"] = bench_kog(torch, S, stream)
+        summary, prec = compare_precisions(torch, S, max(3, min(args.steps, 10)), args.warmup,
+                                           stream)
+        line["fp32_vs_fp64"] = summary
+        line["config"]["compare"] = (
+            "same n=2^26 inputs: FP64 %.1f G/s (%.2f of FP64 pipe); FP32 %.1f G/s (%.2f of HBM), "
+            "sigma'_min err vs FP64 up to %.3g u; FP32 + FP64 tangent step %.1f G/s (%.2f of HBM), "
+            "sigma'_max err <= %.1f u, sigma'_min <= %.1f u; FP32 + full FP64 re-run %.1f G/s, "
+            "sigma'_min <= %.1f u (u = 2^-24)" % (
+                summary["fp64_matrices_per_s"] / 1e9, summary["fp64_fp64_pipe_frac"],
+                summary["fp32_plain_matrices_per_s"] / 1e9, summary["fp32_plain_hbm_frac"],
+                summary["fp32_plain_smin_err_max_u"],
+                summary["fp32_tan64_matrices_per_s"] / 1e9, summary["fp32_tan64_hbm_frac"],
+                summary["fp32_tan64_smax_err_max_u"], summary["fp32_tan64_smin_err_max_u"],
+                summary["fp32_rerun_matrices_per_s"] / 1e9, summary["fp32_rerun_smin_err_max_u"]))
+        report = {"precision": prec,
+                  "complex128": bench_complex128(torch, S, stream),
+                  "multi_batch": bench_multi(torch, S, stream),
+                  "differentiation": bench_grad(torch, S, stream),
+                  "variants": bench_variants(torch, S, stream),
+                  "kogbetliantz_step": bench_kog(torch, S, stream)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(A, W["rows"])
+        line["cpu_baseline"] = cpu_baseline(A, W)
     if dist is not None:
         dist.destroy_process_group()
     if rank == 0:
+        if report is not None:
+            # the supplementary measurements: a file, or one JSON line on stderr
+            if args.report:
+                with open(args.report, "w") as f:
+                    json.dump(report, f, indent=1)
+            else:
+                print(json.dumps({"report": report}), file=sys.stderr, flush=True)
         print(json.dumps(line), flush=True)
 
 

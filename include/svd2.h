@@ -58,6 +58,11 @@ typedef struct CUstream_st *svd2_stream_t;
 
 #define SVD2_S_ZERO INT32_MAX      /* s of the all-zero matrix (Eq. 2: s = DBL_MAX) */
 #define SVD2_BACKSCALE 1u          /* store Sigma = 2^-s Sigma' and s = 0 (Fig. 1)  */
+/* Assemble U by Eq. 31 -- from sin = cos tan of the angles (Sec. 7) -- in
+ * place of the tangent form of Eq. 29 (the same matrix in exact arithmetic;
+ * V, Sigma' and s are unchanged).  Accepted by svd2_batch_{d,z,s,c} and
+ * svd2_batch_host (ops 0 - 3) only; other entry points return SVD2_EINVAL. */
+#define SVD2_SINE 2u
 
 /*
  * Real FP64: n matrices.  A[4], U[4], V[4] hold device pointers to n doubles
@@ -321,7 +326,7 @@ int svd2_bwd_c(int64_t n, const float *const U[8], const float *const V[8],
  *
  * svd2_multi_plan_bytes(nbatch): device bytes of a plan for nbatch batches.
  * svd2_multi_prepare: writes the plan for this launch shape (block a multiple
- *   of 32 in 32..512, mpt in {1, 2}, unroll in {1, 2}) to the caller-owned
+ *   of 32 in 32..1024, mpt in {1, 2, 4}, unroll in {1, 2}) to the caller-owned
  *   device buffer `plan` (16-byte aligned) with a synchronous copy, and returns
  *   the tile count in *total_tiles (may be NULL).  descs is a host array.
  * svd2_multi_run: one launch per kind over the plan, then the fix-up pass
@@ -363,13 +368,14 @@ int svd2_graph_destroy(void *graph_exec);
 
 /*
  * Autotuner.  svd2_autotune_fwd times the forward kernel of op (0 = d, 1 = z,
- * 2 = s, 3 = c) on the caller's batch (arguments as for svd2_batch_*) for
- * every block in {64, 128, 256, 512}, mpt in {1, 2, 4}, unroll in {1, 2} and
- * waves in {0, 4}, `reps` timed launches each after one warm-up launch, sets
- * the fastest as the op's launch shape and returns it with its time per launch
- * (ms).  svd2_multi_autotune does the same for the persistent multi-batch
- * launch (block in {64, 128, 256, 512}, mpt and unroll in {1, 2}), leaving
- * `plan` prepared for the winning shape.  Both synchronise the stream, write
+ * 2 = s, 3 = c, 4 = svd2_batch_s_tan64 at SVD2_TAN64_TAU_LOG2) on the caller's
+ * batch (arguments as for svd2_batch_*) for every block in {64, 128, 256,
+ * 512, 1024} that the op admits (see svd2_set_launch), mpt in {1, 2, 4},
+ * unroll in {1, 2} and waves in {0, 4}, `reps` timed launches each after one
+ * warm-up launch, sets the fastest as the op's launch shape and returns it
+ * with its time per launch (ms).  svd2_multi_autotune does the same for the
+ * multi-batch launch (block in {64, 128, 256, 512, 1024}, mpt in {1, 2, 4},
+ * unroll in {1, 2}), leaving `plan` prepared for the winning shape.  Both synchronise the stream, write
  * the outputs (as a normal call would) and allocate nothing on the device.
  */
 typedef struct svd2_tune_result {
@@ -406,8 +412,11 @@ int svd2_batch_host(int op, int64_t n, const void *const *A, void *const *U, voi
                     svd2_stream_t stream);
 
 /*
- * Launch shape of the forward kernels.  op: 0 = d, 1 = z, 2 = s, 3 = c.
- * block: threads per block (a multiple of 32, 32..512); mpt: matrices per
+ * Launch shape of the forward kernels.  op: 0 = d, 1 = z, 2 = s, 3 = c,
+ * 4 = svd2_batch_s_tan64 (the tangent-step kernel has its own shape; the
+ * re-run forms use those of ops 2 and 3).  block: threads per block (a
+ * multiple of 32, 32..1024; 32..512 for op 2, whose kernel may use up to 128
+ * registers per thread); mpt: matrices per
  * thread per load (1, 2 or 4); unroll: load groups in flight per thread (1 or
  * 2); waves: resident-grid multiples (grid = waves x SMs x resident blocks per
  * SM, capped by the work; 0 = as many blocks as the work needs).  The setting

@@ -38,7 +38,12 @@ struct Launch {
   int waves;    // grid = waves * SMs * resident blocks per SM (0: cover the work)
 };
 
-enum Op { kOpD = 0, kOpZ = 1, kOpS = 2, kOpC = 3, kNumOps = 4 };
+// op 4: the real FP32 form with the FP64 tangent step (its own launch shape)
+enum Op { kOpD = 0, kOpZ = 1, kOpS = 2, kOpC = 3, kOpSTan64 = 4, kNumOps = 5 };
+// Largest block size of op's batch kernel (its launch bounds): 1024 where the
+// kernel is held to 64 registers anyway (FP64, complex, the tangent step),
+// 512 for the plain real FP32 kernel, which may use up to 128.
+inline int max_block(int op) { return op == kOpS ? 512 : 1024; }
 Launch get_launch(int op);
 
 // Grid size for `units` work items of `block` threads each, capped as above.

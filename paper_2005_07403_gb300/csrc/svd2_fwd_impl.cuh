@@ -68,15 +68,16 @@ __device__ __forceinline__ void backscale(Ar &ar, T &smax, T &smin, int32_t &s) 
   s = 0;
 }
 
-// One matrix with the given arithmetic policy (Sec. 2 - Sec. 7, Eq. 29).
-template <typename T, bool CPLX, typename Ar>
+// One matrix with the given arithmetic policy (Sec. 2 - Sec. 7, Eq. 29; with
+// SINE, U by Eq. 31).
+template <typename T, bool CPLX, bool SINE = false, typename Ar>
 __device__ __forceinline__ void svd2_one(Ar &ar, const T *a, T *u, T *v, T &smax, T &smin,
                                          int32_t &s) {
   int piv;
   if constexpr (CPLX)
-    svd2_cplx<T>(ar, a, u, v, smax, smin, s, piv);
+    svd2_cplx<T, SINE>(ar, a, u, v, smax, smin, s, piv);
   else
-    svd2_real<T>(ar, a, u, v, smax, smin, s, piv);
+    svd2_real<T, SINE>(ar, a, u, v, smax, smin, s, piv);
 }
 
 template <typename T> struct SigmaPair {
@@ -87,7 +88,7 @@ template <typename T> struct SigmaPair {
 // stored over whatever the fast kernel stored for it; returns sigma'_max and
 // sigma'_min before any back-scaling.  The element arrays may live in any
 // address space.
-template <typename T, bool CPLX, bool VALS = false>
+template <typename T, bool CPLX, bool VALS = false, bool SINE = false>
 __device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u, T *const *v,
                                                   T *smax, T *smin, int32_t *s, uint32_t flags,
                                                   int64_t k, int64_t stride = 1) {
@@ -97,7 +98,7 @@ __device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u
 #pragma unroll
   for (int e = 0; e < NA; ++e) ai[e] = a[e][k * stride];
   ExactAr<T> ar;
-  svd2_one<T, CPLX>(ar, ai, uo, vo, sx, sn, so);
+  svd2_one<T, CPLX, SINE>(ar, ai, uo, vo, sx, sn, so);
   const SigmaPair<T> r{sx, sn};
   if (flags & SVD2_BACKSCALE) backscale(sx, sn, so);
   if constexpr (!VALS) {
@@ -127,7 +128,8 @@ struct GroupArOf { using type = HotAr<T, CPLX>; };
 template <>
 struct GroupArOf<float, false, true> { using type = Tan64Ar<HotAr<float, false>>; };
 
-template <typename T, bool CPLX, int M, bool VALS = false, bool MARK = false, bool TAN64 = false>
+template <typename T, bool CPLX, int M, bool VALS = false, bool MARK = false, bool TAN64 = false,
+          bool SINE = false>
 __device__ __forceinline__ unsigned process_group(const FwdArgs<T, CPLX ? 8 : 4> &p, int64_t k0,
                                                   const T (&in)[CPLX ? 8 : 4][M]) {
   constexpr int NA = CPLX ? 8 : 4;
@@ -141,7 +143,7 @@ __device__ __forceinline__ unsigned process_group(const FwdArgs<T, CPLX ? 8 : 4>
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
     typename GroupArOf<T, CPLX, TAN64>::type ar;
     if constexpr (TAN64) ar.tau = p.tau;
-    svd2_one<T, CPLX>(ar, a, u, v, sx[m], sn[m], so[m]);
+    svd2_one<T, CPLX, SINE>(ar, a, u, v, sx[m], sn[m], so[m]);
     bool mark = false;
     if constexpr (MARK) mark = sn[m] < fp<T>::mul(p.tau, sx[m]);
     if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
@@ -185,9 +187,14 @@ template <typename T, bool CPLX, bool VALS>
 __global__ void __launch_bounds__(256) fix_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
   if (*p.redo == 0) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const bool sine = (p.flags & SVD2_SINE) != 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride)
-    if (p.s[k] == kRedoS)
-      exact_one<T, CPLX, VALS>(p.a, p.u, p.v, p.smax, p.smin, p.s, p.flags, k, p.stride);
+    if (p.s[k] == kRedoS) {
+      if (sine)
+        exact_one<T, CPLX, VALS, true>(p.a, p.u, p.v, p.smax, p.smin, p.s, p.flags, k, p.stride);
+      else
+        exact_one<T, CPLX, VALS>(p.a, p.u, p.v, p.smax, p.smin, p.s, p.flags, k, p.stride);
+    }
 }
 
 // Blocks of the fix-up pass: enough to scan a batch quickly when it has work.
@@ -206,10 +213,14 @@ inline unsigned fix_grid(int64_t n) {
 // per SM: at 64 registers it runs 19% faster (56.2 -> 67.0 G matrices/s).
 template <typename T, bool CPLX, bool TAN64 = false>
 constexpr int kMinBlocks = (sizeof(T) == 8 || CPLX || TAN64) ? 2 : 1;
+// The same register budget stated as (threads, 1): 1024 threads for a 64-register
+// kernel (two 512-thread blocks' worth), which also admits 1024-thread blocks.
+template <typename T, bool CPLX, bool TAN64 = false>
+constexpr int kMaxThreads = kMinBlocks<T, CPLX, TAN64> == 2 ? 1024 : 512;
 
 template <typename T, bool CPLX, int M, int UNR, bool VALS = false, bool MARK = false,
-          bool TAN64 = false>
-__global__ void __launch_bounds__(512, (kMinBlocks<T, CPLX, TAN64>))
+          bool TAN64 = false, bool SINE = false>
+__global__ void __launch_bounds__((kMaxThreads<T, CPLX, TAN64>), 1)
     fwd_kernel(const __grid_constant__ FwdArgs<T, CPLX ? 8 : 4> p) {
   constexpr int NA = CPLX ? 8 : 4;
   unsigned nwide = 0;
@@ -229,7 +240,8 @@ __global__ void __launch_bounds__(512, (kMinBlocks<T, CPLX, TAN64>))
 #pragma unroll
     for (int r = 0; r < UNR; ++r) {
       const int64_t g = g0 + r * stride;
-      if (g < ngroups) nwide += process_group<T, CPLX, M, VALS, MARK, TAN64>(p, g * M, in[r]);
+      if (g < ngroups)
+        nwide += process_group<T, CPLX, M, VALS, MARK, TAN64, SINE>(p, g * M, in[r]);
     }
   }
   // the n mod M tail, one matrix per thread
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(512, (kMinBlocks<T, CPLX, TAN64>))
     T in1[NA][1];
 #pragma unroll
     for (int e = 0; e < NA; ++e) in1[e][0] = p.a[e][k];
-    nwide += process_group<T, CPLX, 1, VALS, MARK, TAN64>(p, k, in1);
+    nwide += process_group<T, CPLX, 1, VALS, MARK, TAN64, SINE>(p, k, in1);
   }
   if constexpr (TAN64) {
     if (p.count) warp_count_add(p.count, nwide);
@@ -299,9 +311,16 @@ __global__ void __launch_bounds__(256, 2 * kMinBlocks<T, CPLX>) strided_kernel(c
 template <typename T, bool CPLX>
 using FwdKernel = void (*)(const FwdArgs<T, CPLX ? 8 : 4>);
 
-// The values-only kernels exist for one load group in flight only.
+// The values-only kernels and those with the assembly of Eq. 31 exist for one
+// load group in flight only.
 template <typename T, bool CPLX>
-inline FwdKernel<T, CPLX> pick_kernel(int mpt, int unroll, bool vals) {
+inline FwdKernel<T, CPLX> pick_kernel(int mpt, int unroll, bool vals, bool sine = false) {
+  if (sine) {
+    if (mpt == 1) return fwd_kernel<T, CPLX, 1, 1, false, false, false, true>;
+    if (mpt == 2) return fwd_kernel<T, CPLX, 2, 1, false, false, false, true>;
+    if (mpt == 4) return fwd_kernel<T, CPLX, 4, 1, false, false, false, true>;
+    return nullptr;
+  }
 #define SVD2_PICK(M_, U_) \
   if (mpt == M_ && unroll == U_) return fwd_kernel<T, CPLX, M_, U_, false>;
   if (!vals) {
@@ -324,7 +343,9 @@ inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *con
                       T *smin, int32_t *s, uint32_t flags, cudaStream_t stream,
                       FwdArgs<T, CPLX ? 8 : 4> &p, bool vals = false, int64_t stride = 1) {
   constexpr int NA = CPLX ? 8 : 4;
-  if (n < 0 || stride < 1 || (flags & ~SVD2_BACKSCALE)) return SVD2_EINVAL;
+  if (n < 0 || stride < 1 || (flags & ~(SVD2_BACKSCALE | SVD2_SINE))) return SVD2_EINVAL;
+  // Eq. 31 is an assembly of U: for the split layout's full forms only
+  if ((flags & SVD2_SINE) && (stride > 1 || vals)) return SVD2_EINVAL;
   if (n == 0) return SVD2_OK;
   if (!A || (!vals && (!Uo || !Vo)) || !smax || !smin || !s) return SVD2_EINVAL;
   bool vec_ok = stride == 1 && aligned(smax, 16) && aligned(smin, 16) && aligned(s, 16);
@@ -356,9 +377,10 @@ inline int launch_fwd(int op, int64_t n, const T *const *A, T *const *Uo, T *con
     grid = want < 0x7fffffffLL ? want : 0x7fffffffLL;
   } else {
     Launch L = get_launch(op);
+    const bool sine = (flags & SVD2_SINE) && !vals;
     if (!vec_ok) L.mpt = 1;
-    if (vals) L.unroll = 1;
-    k = pick_kernel<T, CPLX>(L.mpt, L.unroll, vals);
+    if (vals || sine) L.unroll = 1;
+    k = pick_kernel<T, CPLX>(L.mpt, L.unroll, vals, sine);
     if (!k) return SVD2_EINVAL;
     int resident = 0;
     SVD2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, L.block, 0));

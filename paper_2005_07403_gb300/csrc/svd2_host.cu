@@ -33,9 +33,6 @@ struct Stage {
   bool init = false;
 };
 
-// op code of svd2_batch_s_tan64 (at the default threshold) for host batches
-constexpr int kHostOpSTan64 = 4;
-
 std::mutex g_mu;
 Stage g_stage[64];
 
@@ -76,7 +73,7 @@ int launch(int op, int64_t n, const void *const *A, void *const *U, void *const 
     case 2:
       return svd2_batch_s(n, (const float *const *)A, (float *const *)U, (float *const *)V,
                           (float *)smax, (float *)smin, s, flags, stream);
-    case kHostOpSTan64:
+    case svd2::kOpSTan64:
       return svd2_batch_s_tan64(n, (const float *const *)A, (float *const *)U,
                                 (float *const *)V, (float *)smax, (float *)smin, s,
                                 SVD2_TAN64_TAU_LOG2, flags, nullptr, stream);
@@ -105,7 +102,7 @@ using namespace svd2;
 extern "C" int svd2_batch_host(int op, int64_t n, const void *const *A, void *const *U,
                                void *const *V, void *smax, void *smin, int32_t *s,
                                uint32_t flags, int64_t chunk, svd2_stream_t stream) {
-  if (op < 0 || op > kHostOpSTan64 || n < 0 || chunk < 0 || (flags & ~SVD2_BACKSCALE))
+  if (op < 0 || op >= kNumOps || n < 0 || chunk < 0 || (flags & ~(SVD2_BACKSCALE | SVD2_SINE)))
     return SVD2_EINVAL;
   if (n == 0) return SVD2_OK;
   const int na = (op == kOpZ || op == kOpC) ? 8 : 4;

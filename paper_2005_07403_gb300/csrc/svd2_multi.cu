@@ -113,7 +113,9 @@ __device__ __forceinline__ void multi_group(const MultiBatch &b, int64_t k0, int
 }
 
 template <bool CPLX, int M, int UNR>
-__global__ void __launch_bounds__(512, 2) multi_kernel(const unsigned char *plan) {
+// (1024, 1): the 64-register budget of two 512-thread blocks per SM, stated so
+// that 1024-thread blocks are admitted too.
+__global__ void __launch_bounds__(1024, 1) multi_kernel(const unsigned char *plan) {
   const MultiPlanHeader &h = *reinterpret_cast<const MultiPlanHeader *>(plan);
   const MultiBatch *batches = reinterpret_cast<const MultiBatch *>(plan + kPlanHeader);
   const int b_end = CPLX ? h.nbatch : h.nreal;
@@ -186,6 +188,8 @@ static MultiKernel pick_multi(int mpt, int unroll) {
   if (mpt == 1 && unroll == 2) return multi_kernel<CPLX, 1, 2>;
   if (mpt == 2 && unroll == 1) return multi_kernel<CPLX, 2, 1>;
   if (mpt == 2 && unroll == 2) return multi_kernel<CPLX, 2, 2>;
+  if (mpt == 4 && unroll == 1) return multi_kernel<CPLX, 4, 1>;
+  if (mpt == 4 && unroll == 2) return multi_kernel<CPLX, 4, 2>;
   return nullptr;
 }
 
@@ -212,7 +216,7 @@ extern "C" int svd2_multi_prepare(const svd2_batch_desc *descs, int32_t nbatch, 
                                   int mpt, int unroll, void *plan, size_t plan_bytes,
                                   int64_t *total_tiles) {
   if (nbatch < 0 || !plan || (nbatch > 0 && !descs)) return SVD2_EINVAL;
-  if (block < 32 || block > 512 || block % 32 || !pick_multi<false>(mpt, unroll)) return SVD2_EINVAL;
+  if (block < 32 || block > 1024 || block % 32 || !pick_multi<false>(mpt, unroll)) return SVD2_EINVAL;
   if (plan_bytes < svd2_multi_plan_bytes(nbatch) || !aligned(plan, 16)) return SVD2_EINVAL;
   const int64_t per_tile = (int64_t)block * mpt * unroll;
   unsigned char *host = new (std::nothrow) unsigned char[svd2_multi_plan_bytes(nbatch)];
@@ -301,7 +305,7 @@ static int multi_grid(MultiKernel k, int block, int grid, int64_t tiles, int *ou
 static int multi_launch(const void *plan, int block, int mpt, int unroll, int grid,
                         cudaStream_t st) {
   const MultiKernel kr = pick_multi<false>(mpt, unroll), kz = pick_multi<true>(mpt, unroll);
-  if (!kr || !kz || block < 32 || block > 512 || block % 32 || grid < 0) return SVD2_EINVAL;
+  if (!kr || !kz || block < 32 || block > 1024 || block % 32 || grid < 0) return SVD2_EINVAL;
   int64_t tr = -1, tz = -1;
   {
     std::lock_guard<std::mutex> g(g_tiles_mu);
@@ -341,7 +345,7 @@ extern "C" int svd2_multi_run(const void *plan, int block, int mpt, int unroll, 
 extern "C" int svd2_multi_graph_create(const void *plan, int block, int mpt, int unroll, int grid,
                                        void **graph_exec) {
   if (!graph_exec || !plan || !aligned(plan, 16)) return SVD2_EINVAL;
-  if (!pick_multi<false>(mpt, unroll) || block < 32 || block > 512 || block % 32 || grid < 0)
+  if (!pick_multi<false>(mpt, unroll) || block < 32 || block > 1024 || block % 32 || grid < 0)
     return SVD2_EINVAL;
   cudaStream_t cs = nullptr;
   SVD2_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

@@ -35,6 +35,7 @@ static Launch g_launch[kNumOps] = {
     {512, 1, 1, 0},   // z
     {512, 2, 1, 4},   // s
     {256, 2, 1, 0},   // c
+    {1024, 2, 1, 4},  // s with the FP64 tangent step
 };
 
 Launch get_launch(int op) {
@@ -100,7 +101,7 @@ using namespace svd2;
 
 extern "C" int svd2_set_launch(int op, int block, int mpt, int unroll, int waves) {
   if (op < 0 || op >= kNumOps) return SVD2_EINVAL;
-  if (block < 32 || block > 512 || block % 32) return SVD2_EINVAL;
+  if (block < 32 || block > max_block(op) || block % 32) return SVD2_EINVAL;
   if (mpt != 1 && mpt != 2 && mpt != 4) return SVD2_EINVAL;
   if (unroll != 1 && unroll != 2) return SVD2_EINVAL;
   if (waves < 0 || waves > 1024) return SVD2_EINVAL;

@@ -89,7 +89,7 @@ extern "C" int svd2_batch_s_tan64(int64_t n, const float *const A[4], float *con
   p.stride = 1;
   p.tau = ldexpf(1.0f, tau_log2);
   p.count = count;
-  Launch L = get_launch(kOpS);
+  Launch L = get_launch(kOpSTan64);
   if (!vec_ok) L.mpt = 1;
   FwdKernel<float, false> k = pick_tan64(L.mpt, L.unroll);
   if (!k) return SVD2_EINVAL;

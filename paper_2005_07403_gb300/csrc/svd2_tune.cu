@@ -28,6 +28,10 @@ int call_fwd(int op, int64_t n, const void *const *A, void *const *U, void *cons
     case 3:
       return svd2_batch_c(n, (const float *const *)A, (float *const *)U, (float *const *)V,
                           (float *)smax, (float *)smin, s, 0, stream);
+    case svd2::kOpSTan64:
+      return svd2_batch_s_tan64(n, (const float *const *)A, (float *const *)U,
+                                (float *const *)V, (float *)smax, (float *)smin, s,
+                                SVD2_TAN64_TAU_LOG2, 0, nullptr, stream);
     default:
       return SVD2_EINVAL;
   }
@@ -76,7 +80,8 @@ extern "C" int svd2_autotune_fwd(int op, int64_t n, const void *const *A, void *
   Events ev;
   if (ev.err != cudaSuccess) return record_cuda_error(ev.err);
   const Launch saved = get_launch(op);
-  static const int blocks[] = {64, 128, 256, 512};
+  // block sizes above the op's kernel limit are refused by set_launch and skipped
+  static const int blocks[] = {64, 128, 256, 512, 1024};
   static const int mpts[] = {1, 2, 4};
   static const int unrolls[] = {1, 2};
   static const int waves[] = {0, 4};
@@ -108,8 +113,8 @@ extern "C" int svd2_multi_autotune(const svd2_batch_desc *descs, int32_t nbatch,
   const cudaStream_t st = (cudaStream_t)stream;
   Events ev;
   if (ev.err != cudaSuccess) return record_cuda_error(ev.err);
-  static const int blocks[] = {64, 128, 256, 512};
-  static const int mpts[] = {1, 2};
+  static const int blocks[] = {64, 128, 256, 512, 1024};
+  static const int mpts[] = {1, 2, 4};
   static const int unrolls[] = {1, 2};
   svd2_tune_result b{0, 0, 0, 0, FLT_MAX};
   for (int bl : blocks)

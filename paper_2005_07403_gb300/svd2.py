@@ -29,8 +29,9 @@ ETOOBIG = -4
 NOALLOC_MAX_N = 1 << 20
 S_ZERO = 2**31 - 1
 BACKSCALE = 1
+SINE = 2
 
-OPS = {"d": 0, "z": 1, "s": 2, "c": 3}
+OPS = {"d": 0, "z": 1, "s": 2, "c": 3, "s_tan64": 4}
 
 _lock = threading.Lock()
 _lib = None
@@ -210,10 +211,11 @@ def empty_result(rows: int, n: int, dtype, device) -> Svd2Result:
 
 
 def svd2(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = None,
-         stream: int | None = None) -> Svd2Result:
+         stream: int | None = None, sine: bool = False) -> Svd2Result:
     """Batched 2x2 SVD of the split-layout batch ``A`` (shape (4, n) or (8, n),
-    float64 or float32, on a CUDA device).  Asynchronous on ``stream`` (default:
-    torch's current stream)."""
+    float64 or float32, on a CUDA device).  ``sine``: U assembled by Eq. 31
+    (sines and cosines) instead of Eq. 29.  Asynchronous on ``stream``
+    (default: torch's current stream)."""
     rows, n = A.shape
     kind = _kind(rows, A.dtype)
     a_ptrs = _rows(A, "A")
@@ -224,7 +226,8 @@ def svd2(A: torch.Tensor, *, backscale: bool = False, out: Svd2Result | None = N
     h = current_stream_handle(A.device) if stream is None else stream
     f = getattr(lib(), "svd2_batch_" + kind)
     rc = f(n, ptr_array(a_ptrs), ptr_array(u_ptrs), ptr_array(v_ptrs), out.smax.data_ptr(),
-           out.smin.data_ptr(), out.s.data_ptr(), BACKSCALE if backscale else 0, h)
+           out.smin.data_ptr(), out.s.data_ptr(),
+           (BACKSCALE if backscale else 0) | (SINE if sine else 0), h)
     check(rc, "svd2_batch_" + kind)
     return out
 
@@ -500,11 +503,17 @@ def svd2_bwd(U, V, s1, s2, gU=None, gV=None, g1=None, g2=None, rel_delta=None,
     return out
 
 
-def autotune_fwd(A: torch.Tensor, out: Svd2Result | None = None, reps: int = 5) -> dict:
+def autotune_fwd(A: torch.Tensor, out: Svd2Result | None = None, reps: int = 5,
+                 form: str = "plain") -> dict:
     """Time every launch shape of A's form on A (svd2_autotune_fwd) and keep the
-    fastest as that form's launch shape.  Returns the winning shape."""
+    fastest as that form's launch shape.  ``form``: "plain", or "tan64" for the
+    real FP32 form with the FP64 tangent step.  Returns the winning shape."""
     rows, n = A.shape
     kind = _kind(rows, A.dtype)
+    if form == "tan64":
+        if kind != "s":
+            raise TypeError("the FP64 tangent step form takes real float32 input")
+        kind = "s_tan64"
     if out is None:
         out = empty_result(rows, n, A.dtype, A.device)
     res = TuneResult()

@@ -42,11 +42,13 @@ def _store(d: dict):
 
 
 def tune(A: torch.Tensor, out: S.Svd2Result | None = None, reps: int = 5,
-         use_cache: bool = True) -> dict:
+         use_cache: bool = True, form: str = "plain") -> dict:
     """Launch shape for A's form and size: from the cache, else measured by the
-    native tuner on A (and cached).  The shape is applied with set_launch."""
+    native tuner on A (and cached).  The shape is applied with set_launch.
+    ``form``: "plain" or "tan64" (the FP32 form with the FP64 tangent step,
+    which has its own launch shape)."""
     rows, n = A.shape
-    kind = S._kind(rows, A.dtype)
+    kind = S._kind(rows, A.dtype) + ("_tan64" if form == "tan64" else "")
     key = _key(kind, n)
     with _lock:
         cache = _load()
@@ -54,7 +56,7 @@ def tune(A: torch.Tensor, out: S.Svd2Result | None = None, reps: int = 5,
     if hit is not None:
         S.set_launch(kind, hit["block"], hit["mpt"], hit["unroll"], hit["waves"])
         return dict(hit, cached=True)
-    best = S.autotune_fwd(A, out, reps)
+    best = S.autotune_fwd(A, out, reps, form=form)
     with _lock:
         cache = _load()
         cache[key] = best

@@ -79,6 +79,11 @@ def test_launch_table_roundtrip_and_validation():
         assert S.get_launch("s") == (128, 2, 2, 3)
         assert L.svd2_set_launch(2, 100, 1, 1, 0) == S.EINVAL     # not a multiple of 32
         assert L.svd2_set_launch(2, 1024, 1, 1, 0) == S.EINVAL    # above 512
+        for op in (0, 1, 3, 4):                                     # 64-register kernels
+            saved = S.get_launch({0: "d", 1: "z", 3: "c", 4: "s_tan64"}[op])
+            assert L.svd2_set_launch(op, 1024, 1, 1, 0) == S.OK
+            assert L.svd2_set_launch(op, 1056, 1, 1, 0) == S.EINVAL
+            assert L.svd2_set_launch(op, *saved) == S.OK
         assert L.svd2_set_launch(2, 128, 3, 1, 0) == S.EINVAL     # mpt
         assert L.svd2_set_launch(9, 128, 1, 1, 0) == S.EINVAL     # op
     finally:

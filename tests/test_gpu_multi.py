@@ -39,7 +39,8 @@ def _check_all(mb, hosts, what):
         assert_same(g, oracle.svd2(A), f"{what} batch {i}")
 
 
-@pytest.mark.parametrize("shape", [(256, 1, 1), (64, 2, 2), (512, 1, 2), (128, 2, 1)])
+@pytest.mark.parametrize("shape", [(256, 1, 1), (64, 2, 2), (512, 1, 2), (128, 2, 1),
+                                   (1024, 1, 1), (128, 4, 1), (256, 4, 2)])
 def test_multi_matches_oracle_per_batch(shape):
     hosts = _batches(40, 3)
     mb = S.MultiBatch([torch.from_numpy(A).cuda() for A in hosts], *shape)
@@ -97,7 +98,7 @@ def test_multi_autotune_picks_a_valid_shape():
     hosts = _batches(30, 6, hi=20000)
     mb = S.MultiBatch([torch.from_numpy(A).cuda() for A in hosts])
     best = mb.autotune(reps=2)
-    assert best["block"] in (64, 128, 256, 512) and best["mpt"] in (1, 2)
+    assert best["block"] in (64, 128, 256, 512, 1024) and best["mpt"] in (1, 2, 4)
     assert best["ms"] > 0
     mb.run()
     _check_all(mb, hosts, "tuned")

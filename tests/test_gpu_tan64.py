@@ -40,12 +40,16 @@ def test_tan64_matches_oracle(tau):
 def test_tan64_every_launch_shape(mpt, unroll):
     A32, _ = inputs.real_fp32_illcond(2**16 + 5, seed=3302)
     o = oracle.svd2_tan64(A32, -4)
-    old = S.get_launch("s")
+    old = S.get_launch("s_tan64")
     try:
-        S.set_launch("s", 256, mpt, unroll, 0)
+        S.set_launch("s_tan64", 256, mpt, unroll, 0)
         g, cnt = run(A32, -4)
+        S.set_launch("s_tan64", 1024, mpt, unroll, 4)
+        g2, cnt2 = run(A32, -4)
     finally:
-        S.set_launch("s", *old)
+        S.set_launch("s_tan64", *old)
+    assert_same(g2, o, f"s_tan64 block 1024 mpt={mpt} unroll={unroll}")
+    assert cnt2 == o["count"]
     assert_same(g, o, f"s_tan64 mpt={mpt} unroll={unroll}")
     assert cnt == o["count"]
 
@@ -144,3 +148,23 @@ def test_tan64_full_size_sampled():
     assert (np.abs(bx - o64["smax"]) / o64["smax"]).max() <= 8 * u
     w = o["wide"].astype(bool) & (o64["smin"] > 0)
     assert (np.abs(bn - o64["smin"])[w] / o64["smin"][w]).max() <= 8 * u
+
+
+def test_tan64_autotuner_keeps_results():
+    """The tuner times the tangent-step kernel under its own launch shape (op
+    4), leaves the plain FP32 shape alone, and the tuned kernel still matches
+    the oracle bit for bit."""
+    from paper_2005_07403_gb300 import tune
+    A32, _ = inputs.real_fp32_illcond(50001, seed=3308)
+    Ad = torch.from_numpy(A32).cuda()
+    saved, saved_s = S.get_launch("s_tan64"), S.get_launch("s")
+    try:
+        t = tune.tune(Ad, reps=1, use_cache=False, form="tan64")
+        assert S.get_launch("s_tan64") == (t["block"], t["mpt"], t["unroll"], t["waves"])
+        assert S.get_launch("s") == saved_s
+        g, cnt = run(A32, -3)
+        o = oracle.svd2_tan64(A32, -3)
+        assert_same(g, o, "tan64 tuned")
+        assert cnt == o["count"]
+    finally:
+        S.set_launch("s_tan64", *saved)
