@@ -435,8 +435,11 @@ int svd2_get_launch(int op, int *block, int *mpt, int *unroll, int *waves);
  * (op 0: x[i] / y[i]; op 1: sqrt(x[i]); op 2: x[i] rounded to float, stored
  * widened exactly; op 3: the float whose bit pattern is the low 32 bits of
  * x[i], widened to double -- the conversions of the FP32 form's FP64 re-run;
- * y unused for ops 1-3).  All pointers are device arrays of n doubles.  The
- * two must agree bit for bit (NaNs: any NaN).
+ * op 4: x[i] and y[i] rounded to float, then the double quotient of the two
+ * floats completed from their float quotient, as the tangent step of
+ * svd2_batch_s_tan64 computes it, NaN where its operands are outside the
+ * routine's domain; y unused for ops 1-3).  All pointers are device arrays of
+ * n doubles.  The two must agree bit for bit (NaNs: any NaN).
  */
 int svd2_arith_check(int op, int64_t n, const double *x, const double *y, double *lib,
                      double *hw, svd2_stream_t stream);

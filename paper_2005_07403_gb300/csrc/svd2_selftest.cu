@@ -23,10 +23,18 @@ __global__ void arith_check_kernel(int op, int64_t n, const double *x, const dou
     } else if (op == 2) {
       lib[i] = (double)svd2::sfp::d2f(a);
       hw[i] = (double)__double2float_rn(a);
-    } else {
+    } else if (op == 3) {
       const float f = __uint_as_float((unsigned)__double2loint(a));
       lib[i] = svd2::sfp::f2d(f);
       hw[i] = (double)f;
+    } else {
+      // the double quotient of two floats (x, y rounded to float) completed from
+      // their float quotient; NaN where it flags the operands
+      const float fa = __double2float_rn(a), fb = __double2float_rn(y[i]);
+      unsigned flag = 0;
+      const double q = svd2::sfp::div_ff(fa, fb, __fdiv_rn(fa, fb), flag);
+      lib[i] = flag ? __longlong_as_double(0x7ff8000000000000ll) : q;
+      hw[i] = __ddiv_rn((double)fa, (double)fb);
     }
   }
 }
@@ -92,10 +100,10 @@ extern "C" int svd2_fp32_selfcheck(int op, uint64_t begin, uint64_t count, void 
 
 extern "C" int svd2_arith_check(int op, int64_t n, const double *x, const double *y, double *lib,
                                 double *hw, svd2_stream_t stream) {
-  if (op < 0 || op > 3) return SVD2_EINVAL;
+  if (op < 0 || op > 4) return SVD2_EINVAL;
   if (n < 0) return SVD2_EINVAL;
   if (n == 0) return SVD2_OK;
-  if (!x || !lib || !hw || (op == 0 && !y)) return SVD2_EINVAL;
+  if (!x || !lib || !hw || ((op == 0 || op == 4) && !y)) return SVD2_EINVAL;
   const int grid = 8 * svd2::sm_count();
   arith_check_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(op, n, x, y, lib, hw);
   SVD2_CUDA_TRY(cudaGetLastError());

@@ -440,12 +440,14 @@ def rerun_count(workspace: torch.Tensor) -> int:
 
 def arith_check(op: str, x: torch.Tensor, y: torch.Tensor | None = None):
     """The library's double division ("div"), square root ("sqrt"), rounding to
-    float ("d2f", results widened exactly) or widening of the float in the low
-    32 bits of each element ("f2d") next to the hardware instruction, on
-    float64 CUDA tensors; returns (lib, hw)."""
+    float ("d2f", results widened exactly), widening of the float in the low
+    32 bits of each element ("f2d") or double quotient of two floats completed
+    from their float quotient ("div_ff": x, y rounded to float first; NaN
+    where the operands are outside its domain) next to the hardware
+    instruction, on float64 CUDA tensors; returns (lib, hw)."""
     lib_out = torch.empty_like(x)
     hw_out = torch.empty_like(x)
-    code = {"div": 0, "sqrt": 1, "d2f": 2, "f2d": 3}[op]
+    code = {"div": 0, "sqrt": 1, "d2f": 2, "f2d": 3, "div_ff": 4}[op]
     rc = lib().svd2_arith_check(code, x.numel(), x.data_ptr(),
                                 None if y is None else y.data_ptr(), lib_out.data_ptr(),
                                 hw_out.data_ptr(), current_stream_handle(x.device))

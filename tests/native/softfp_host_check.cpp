@@ -87,6 +87,24 @@ static void chk_f2d(uint32_t b) {
   }
 }
 
+// the float-quotient division: where it does not flag the operands, the CPU's
+// double quotient of the widened floats, given the CPU's float quotient
+static long long ff_checked = 0;
+static void chk_div_ff(float a, float b) {
+  const float q32 = a / b;
+  unsigned flag = 0;
+  const double r = svd2::sfp::div_ff(a, b, q32, flag), h = (double)a / (double)b;
+  ++checked;
+  if (!flag) ++ff_checked;
+  if (!flag && dbits(r) != dbits(h)) {
+    if (bad < 10) std::printf("div_ff mismatch a=%a b=%a soft=%a hw=%a\n", (double)a, (double)b, r, h);
+    ++bad;
+  }
+}
+static float fmk(uint32_t sign, uint32_t bexp, uint32_t frac) {
+  return svd2::sfp::fval((sign << 31) | ((bexp & 0xffu) << 23) | (frac & 0x7fffffu));
+}
+
 // a double with the given biased exponent and mantissa bits
 static double mk(uint64_t sign, uint64_t bexp, uint64_t frac) {
   return dval((sign << 63) | ((bexp & 0x7ff) << 52) | (frac & 0xfffffffffffffull));
@@ -114,7 +132,29 @@ int main(int argc, char **argv) {
   for (int sa = 0; sa < 2; ++sa)
     for (int sb = 0; sb < 2; ++sb)
       for (uint64_t e : {1ull, 1023ull, 2046ull}) chk_div(mk(sa, 0, 0), mk(sb, e, 0x123456789abcull));
+  // float quotients: zero numerators, exact quotients, the binade edges
+  for (uint32_t fb : {0u, 1u, 0x7fffffu, 0x400000u, 0x555555u})
+    for (uint32_t eb : {1u, 64u, 127u, 200u, 254u}) {
+      chk_div_ff(0.0f, fmk(0, eb, fb));
+      chk_div_ff(-0.0f, fmk(1, eb, fb));
+      for (uint32_t fa : {0u, 1u, 0x7fffffu, 0x400000u, fb, fb ^ 1u, fb + 1u})
+        for (uint32_t ea : {1u, 100u, 127u, 128u, 254u}) chk_div_ff(fmk(0, ea, fa), fmk(0, eb, fb));
+    }
   for (long long i = 0; i < n; ++i) {
+    {
+      // float quotients: random significands, exponents near each other and
+      // anywhere, numerators below the divisor (the method's use), small
+      // integer multiples (exact quotients), runs of ones
+      const uint32_t r1 = (uint32_t)sm64(s), r2 = (uint32_t)sm64(s), r3 = (uint32_t)sm64(s);
+      const uint32_t eb = 1 + r3 % 254, ea = 1 + (r3 >> 8) % 254;
+      chk_div_ff(fmk(r1 >> 31, ea, r1), fmk(r2 >> 31, eb, r2));
+      const uint32_t en = eb - 40 + (r3 >> 16) % 41;
+      if (en >= 1 && en <= 254) chk_div_ff(fmk(0, en, r1), fmk(0, eb, r2));
+      chk_div_ff(fmk(0, eb, r1 | 0x7ff000u), fmk(0, eb, r2 | 0x7ff000u));
+      const float b = fmk(0, 100 + r3 % 50, r2), k = (float)(1 + r1 % 4096);
+      chk_div_ff(b * k, b);
+      chk_div_ff(fmk(0, eb, 0x7fffffu ^ (1u << (r1 % 23))), fmk(0, eb, r2));
+    }
     // conversions: any float pattern; doubles around the float range (float
     // subnormal results, overflow), with the 29 dropped bits random, exactly
     // half an ulp (ties), or half an ulp +-1
@@ -159,6 +199,7 @@ int main(int argc, char **argv) {
     chk_div(std::nextafter(bb, 0.0), bb);
     chk_div(mk(0, ea, sm64(s)), mk(0, eb, (sm64(s) % 4096) << 40));
   }
+  std::printf("float quotients in domain %lld\n", ff_checked);
   std::printf("checked %lld mismatches %lld\n", checked, bad);
   return bad ? 1 : 0;
 }

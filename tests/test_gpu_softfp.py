@@ -126,3 +126,32 @@ def test_fp32_division_significand_pairs():
         _selfcheck("div_sig", c << 43, 1 << 33)
     r = _selfcheck("div_rand", 0, 1 << 32)
     assert r["checked"] > 1 << 28
+
+
+@pytest.mark.parametrize("cls", ["near", "below", "wide", "exact"])
+def test_float_quotient_division_matches_hardware(cls):
+    """The double quotient of two floats completed from their float quotient
+    (the tangent step of the FP32 form): where it accepts the operands, the
+    hardware double division of the widened floats, bit for bit; it accepts
+    every pair with normal floats and a normal float quotient."""
+    if cls == "near":              # exponents near each other
+        x = _with_exponent(_bits(N, 31), 1000, 1046, 32).float().double()
+        y = _with_exponent(_bits(N, 33), 1000, 1046, 34).float().double()
+    elif cls == "below":           # numerator below the divisor: the method's tan(alpha)
+        y = _with_exponent(_bits(N, 35), 1023, 1060, 36).float().double()
+        x = (y * torch.rand(N, device="cuda", dtype=torch.float64)).float().double()
+    elif cls == "wide":            # the float exponent range
+        x = _with_exponent(_bits(N, 37), 1023 - 126, 1023 + 127, 38).float().double()
+        y = _with_exponent(_bits(N, 39), 1023 - 126, 1023 + 127, 40).float().double()
+    else:                          # exact quotients: small integer multiples
+        y = _with_exponent(_bits(N, 41), 1023, 1030, 42).float().double()
+        k = torch.randint(1, 4096, (N,), device="cuda", dtype=torch.float64)
+        x = (y * k).float().double()
+    lib, hw = S.arith_check("div_ff", x, y)
+    torch.cuda.synchronize()
+    q = (x.float() / y.float()).abs()
+    normal = (x != 0) & (q >= 2.0**-126) & torch.isfinite(q)
+    flagged = torch.isnan(lib)
+    assert not bool(torch.any(flagged & normal)), cls
+    ok = flagged | (lib.view(torch.int64) == hw.view(torch.int64))
+    assert bool(torch.all(ok)), cls
