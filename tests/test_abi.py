@@ -63,7 +63,8 @@ def test_invalid_arguments_rejected_on_host():
     assert L.svd2_batch_interleaved_s(-1, fake, fake, fake, fake, fake, fake, 0, None) == S.EINVAL
     assert L.svd2_batch_interleaved_s(0, None, None, None, None, None, None, 0, None) == S.OK
     # self-tests: unknown op, NULL or misaligned result (checked before any launch)
-    assert L.svd2_arith_check(4, 8, fake, fake, fake, fake, None) == S.EINVAL
+    assert L.svd2_arith_check(5, 8, fake, fake, fake, fake, None) == S.EINVAL
+    assert L.svd2_arith_check(4, 8, fake, None, fake, fake, None) == S.EINVAL   # op 4 needs y
     assert L.svd2_arith_check(0, -1, fake, fake, fake, fake, None) == S.EINVAL
     assert L.svd2_fp32_selfcheck(4, 0, 8, fake, None) == S.EINVAL
     assert L.svd2_fp32_selfcheck(0, 0, 8, None, None) == S.EINVAL
