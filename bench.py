@@ -576,11 +576,11 @@ def bench_multi(torch, S, stream, replays=20):
 
 # The adjoint kernels' algorithmic traffic per matrix: U, V, s1, s2, gU, gV,
 # g1, g2 read and gA written once (real: 20 + 4 values, complex: 36 + 8), and
-# the real FP64 adjoint's FP64 add/mul per matrix counted from its formulas
-# (J and K 12, a and b 2, s1 + s2 1, the gap 5, p and q 6, M 2, U M 12,
-# (U M) V^T 12; its three divisions run on the integer pipe).
+# the real FP64 adjoint's FP64 add/mul/fma per matrix counted from its
+# formulas (J and K 8, a and b 2, s1 + s2 1, the gap 4, p and q 6, M 2, U M 8,
+# (U M) V^T 8; its three divisions run on the integer pipe).
 BWD_BYTES = {"fp64": 24 * 8, "fp32": 24 * 4, "complex128": 44 * 8, "complex64": 44 * 4}
-BWD_FP64_OPS_REAL = 52
+BWD_FP64_OPS_REAL = 39
 
 
 def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):

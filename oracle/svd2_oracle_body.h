@@ -455,10 +455,11 @@ static inline void SFX(adjoint)(const T u[4], const T v[4], T s1, T s2, const T 
 {
     const T u11 = u[0], u21 = u[1], u12 = u[2], u22 = u[3];
     const T v11 = v[0], v21 = v[1], v12 = v[2], v22 = v[3];
-    const T J12 = u11 * gu[2] + u21 * gu[3];
-    const T J21 = u12 * gu[0] + u22 * gu[1];
-    const T K12 = v11 * gv[2] + v21 * gv[3];
-    const T K21 = v12 * gv[0] + v22 * gv[1];
+    /* every two-term dot product as fma(x0, y0, x1 y1) */
+    const T J12 = T_FMA(u11, gu[2], u21 * gu[3]);
+    const T J21 = T_FMA(u12, gu[0], u22 * gu[1]);
+    const T K12 = T_FMA(v11, gv[2], v21 * gv[3]);
+    const T K21 = T_FMA(v12, gv[0], v22 * gv[1]);
     const T a = J12 - J21, b = K12 - K21;
     const T sum = s1 + s2;
     const T inv_sum = sum > (T)0 ? (T)1 / sum : (T)0;
@@ -467,18 +468,18 @@ static inline void SFX(adjoint)(const T u[4], const T v[4], T s1, T s2, const T 
         const T g = (s1 - s2) / s1;
         /* g = 0 (s1 = s2): the safeguard's value there, 0, also at dl = 0,
          * where the formula reads 0/0 */
-        inv_gap = g == (T)0 ? (T)0 : g / (s1 * (g * g + dl * dl));
+        inv_gap = g == (T)0 ? (T)0 : g / (s1 * T_FMA(g, g, dl * dl));
     }
     const T p = (T)0.5 * (a - b) * inv_sum;
     const T q = (T)0.5 * (a + b) * inv_gap;
     const T m11 = g1, m12 = p - q, m21 = -p - q, m22 = g2;
     /* W = U M, then gA = W V^T */
-    const T w11 = u11 * m11 + u12 * m21, w12 = u11 * m12 + u12 * m22;
-    const T w21 = u21 * m11 + u22 * m21, w22 = u21 * m12 + u22 * m22;
-    ga[0] = w11 * v11 + w12 * v12;   /* gA_11 */
-    ga[1] = w21 * v11 + w22 * v12;   /* gA_21 */
-    ga[2] = w11 * v21 + w12 * v22;   /* gA_12 */
-    ga[3] = w21 * v21 + w22 * v22;   /* gA_22 */
+    const T w11 = T_FMA(u11, m11, u12 * m21), w12 = T_FMA(u11, m12, u12 * m22);
+    const T w21 = T_FMA(u21, m11, u22 * m21), w22 = T_FMA(u21, m12, u22 * m22);
+    ga[0] = T_FMA(w11, v11, w12 * v12);   /* gA_11 */
+    ga[1] = T_FMA(w21, v11, w22 * v12);   /* gA_21 */
+    ga[2] = T_FMA(w11, v21, w12 * v22);   /* gA_12 */
+    ga[3] = T_FMA(w21, v21, w22 * v22);   /* gA_22 */
 }
 
 /*
@@ -503,19 +504,20 @@ static inline void SFX(adjoint_cplx)(const T ur[4], const T ui[4], const T vr[4]
                               T s1, T s2, const T gur[4], const T gui[4], const T gvr[4],
                               const T gvi[4], T g1, T g2, T dl, T gar[4], T gai[4])
 {
-    /* J_xy = sum_a conj(u_ax) gu_ay, element (a, x) at a + 2x */
-    const T Jr12 = (ur[0] * gur[2] + ui[0] * gui[2]) + (ur[1] * gur[3] + ui[1] * gui[3]);
-    const T Ji12 = (ur[0] * gui[2] - ui[0] * gur[2]) + (ur[1] * gui[3] - ui[1] * gur[3]);
-    const T Jr21 = (ur[2] * gur[0] + ui[2] * gui[0]) + (ur[3] * gur[1] + ui[3] * gui[1]);
-    const T Ji21 = (ur[2] * gui[0] - ui[2] * gur[0]) + (ur[3] * gui[1] - ui[3] * gur[1]);
-    const T Ji11 = (ur[0] * gui[0] - ui[0] * gur[0]) + (ur[1] * gui[1] - ui[1] * gur[1]);
-    const T Ji22 = (ur[2] * gui[2] - ui[2] * gur[2]) + (ur[3] * gui[3] - ui[3] * gur[3]);
-    const T Kr12 = (vr[0] * gvr[2] + vi[0] * gvi[2]) + (vr[1] * gvr[3] + vi[1] * gvi[3]);
-    const T Ki12 = (vr[0] * gvi[2] - vi[0] * gvr[2]) + (vr[1] * gvi[3] - vi[1] * gvr[3]);
-    const T Kr21 = (vr[2] * gvr[0] + vi[2] * gvi[0]) + (vr[3] * gvr[1] + vi[3] * gvi[1]);
-    const T Ki21 = (vr[2] * gvi[0] - vi[2] * gvr[0]) + (vr[3] * gvi[1] - vi[3] * gvr[1]);
-    const T Ki11 = (vr[0] * gvi[0] - vi[0] * gvr[0]) + (vr[1] * gvi[1] - vi[1] * gvr[1]);
-    const T Ki22 = (vr[2] * gvi[2] - vi[2] * gvr[2]) + (vr[3] * gvi[3] - vi[3] * gvr[3]);
+    /* J_xy = sum_a conj(u_ax) gu_ay, element (a, x) at a + 2x; every four-term
+     * sum as the fma chain x0 y0 + (x1 y1 + (x2 y2 + x3 y3)), innermost a product */
+#define CRE(x, y, a0, b0, a1, b1) T_FMA(x##r[a0], y##r[b0], T_FMA(x##i[a0], y##i[b0], \
+        T_FMA(x##r[a1], y##r[b1], x##i[a1] * y##i[b1])))
+#define CIM(x, y, a0, b0, a1, b1) T_FMA(x##r[a0], y##i[b0], T_FMA(-x##i[a0], y##r[b0], \
+        T_FMA(x##r[a1], y##i[b1], -(x##i[a1] * y##r[b1]))))
+    const T Jr12 = CRE(u, gu, 0, 2, 1, 3), Ji12 = CIM(u, gu, 0, 2, 1, 3);
+    const T Jr21 = CRE(u, gu, 2, 0, 3, 1), Ji21 = CIM(u, gu, 2, 0, 3, 1);
+    const T Ji11 = CIM(u, gu, 0, 0, 1, 1), Ji22 = CIM(u, gu, 2, 2, 3, 3);
+    const T Kr12 = CRE(v, gv, 0, 2, 1, 3), Ki12 = CIM(v, gv, 0, 2, 1, 3);
+    const T Kr21 = CRE(v, gv, 2, 0, 3, 1), Ki21 = CIM(v, gv, 2, 0, 3, 1);
+    const T Ki11 = CIM(v, gv, 0, 0, 1, 1), Ki22 = CIM(v, gv, 2, 2, 3, 3);
+#undef CRE
+#undef CIM
     /* a = J12 - conj(J21), b = K12 - conj(K21) */
     const T ar = Jr12 - Jr21, ai = Ji12 + Ji21;
     const T br = Kr12 - Kr21, bi = Ki12 + Ki21;
@@ -526,7 +528,7 @@ static inline void SFX(adjoint_cplx)(const T ur[4], const T ui[4], const T vr[4]
         const T g = (s1 - s2) / s1;
         /* g = 0 (s1 = s2): the safeguard's value there, 0, also at dl = 0,
          * where the formula reads 0/0 */
-        inv_gap = g == (T)0 ? (T)0 : g / (s1 * (g * g + dl * dl));
+        inv_gap = g == (T)0 ? (T)0 : g / (s1 * T_FMA(g, g, dl * dl));
     }
     const T pr = (T)0.5 * (ar - br) * inv_sum, pi = (T)0.5 * (ai - bi) * inv_sum;
     const T qr = (T)0.5 * (ar + br) * inv_gap, qi = (T)0.5 * (ai + bi) * inv_gap;
@@ -540,14 +542,18 @@ static inline void SFX(adjoint_cplx)(const T ur[4], const T ui[4], const T vr[4]
     for (int x = 0; x < 2; ++x)
         for (int y = 0; y < 2; ++y) {
             const int o = x + 2 * y, u1 = x, u2 = x + 2, m1 = 2 * y, m2 = 2 * y + 1;
-            wr[o] = (ur[u1] * mr[m1] - ui[u1] * mi[m1]) + (ur[u2] * mr[m2] - ui[u2] * mi[m2]);
-            wi[o] = (ur[u1] * mi[m1] + ui[u1] * mr[m1]) + (ur[u2] * mi[m2] + ui[u2] * mr[m2]);
+            wr[o] = T_FMA(ur[u1], mr[m1], T_FMA(-ui[u1], mi[m1],
+                          T_FMA(ur[u2], mr[m2], -(ui[u2] * mi[m2]))));
+            wi[o] = T_FMA(ur[u1], mi[m1], T_FMA(ui[u1], mr[m1],
+                          T_FMA(ur[u2], mi[m2], ui[u2] * mr[m2])));
         }
     /* gA = W V^*: ga_xy = w_x1 conj(v_y1) + w_x2 conj(v_y2) */
     for (int x = 0; x < 2; ++x)
         for (int y = 0; y < 2; ++y) {
             const int o = x + 2 * y, w1 = x, w2 = x + 2, v1 = y, v2 = y + 2;
-            gar[o] = (wr[w1] * vr[v1] + wi[w1] * vi[v1]) + (wr[w2] * vr[v2] + wi[w2] * vi[v2]);
-            gai[o] = (wi[w1] * vr[v1] - wr[w1] * vi[v1]) + (wi[w2] * vr[v2] - wr[w2] * vi[v2]);
+            gar[o] = T_FMA(wr[w1], vr[v1], T_FMA(wi[w1], vi[v1],
+                           T_FMA(wr[w2], vr[v2], wi[w2] * vi[v2])));
+            gai[o] = T_FMA(wi[w1], vr[v1], T_FMA(-wr[w1], vi[v1],
+                           T_FMA(wi[w2], vr[v2], -(wr[w2] * vi[v2]))));
         }
 }

@@ -58,10 +58,11 @@ __global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs<T> p) {
     const T gv11 = ld0(p.gv[0], k), gv21 = ld0(p.gv[1], k);
     const T gv12 = ld0(p.gv[2], k), gv22 = ld0(p.gv[3], k);
     // J12 = (U^T gU)_12, J21 = (U^T gU)_21, likewise K for V
-    const T J12 = F::add(F::mul(u11, gu12), F::mul(u21, gu22));
-    const T J21 = F::add(F::mul(u12, gu11), F::mul(u22, gu21));
-    const T K12 = F::add(F::mul(v11, gv12), F::mul(v21, gv22));
-    const T K21 = F::add(F::mul(v12, gv11), F::mul(v22, gv21));
+    // (every two-term dot product as fma(x0, y0, x1 y1))
+    const T J12 = F::fma(u11, gu12, F::mul(u21, gu22));
+    const T J21 = F::fma(u12, gu11, F::mul(u22, gu21));
+    const T K12 = F::fma(v11, gv12, F::mul(v21, gv22));
+    const T K21 = F::fma(v12, gv11, F::mul(v22, gv21));
     const T a = F::sub(J12, J21), b = F::sub(K12, K21);
     const T sum = F::add(s1, s2);
     const T inv_sum = sum > T(0) ? F::div(T(1), sum) : T(0);
@@ -69,21 +70,21 @@ __global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs<T> p) {
     if (s1 > T(0)) {
       const T g = F::div(F::sub(s1, s2), s1);
       // g = 0: the safeguard's value there (0), also for rel_delta = 0 (0/0)
-      inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
+      inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::fma(g, g, F::mul(p.dl, p.dl))));
     }
     const T pp = F::mul(F::mul(T(0.5), F::sub(a, b)), inv_sum);
     const T qq = F::mul(F::mul(T(0.5), F::add(a, b)), inv_gap);
     const T m11 = ld0(p.g1, k), m22 = ld0(p.g2, k);
     const T m12 = F::sub(pp, qq), m21 = F::sub(b_neg(pp), qq);
     // W = U M, gA = W V^T
-    const T w11 = F::add(F::mul(u11, m11), F::mul(u12, m21));
-    const T w12 = F::add(F::mul(u11, m12), F::mul(u12, m22));
-    const T w21 = F::add(F::mul(u21, m11), F::mul(u22, m21));
-    const T w22 = F::add(F::mul(u21, m12), F::mul(u22, m22));
-    __stcs(p.ga[0] + k, F::add(F::mul(w11, v11), F::mul(w12, v12)));
-    __stcs(p.ga[1] + k, F::add(F::mul(w21, v11), F::mul(w22, v12)));
-    __stcs(p.ga[2] + k, F::add(F::mul(w11, v21), F::mul(w12, v22)));
-    __stcs(p.ga[3] + k, F::add(F::mul(w21, v21), F::mul(w22, v22)));
+    const T w11 = F::fma(u11, m11, F::mul(u12, m21));
+    const T w12 = F::fma(u11, m12, F::mul(u12, m22));
+    const T w21 = F::fma(u21, m11, F::mul(u22, m21));
+    const T w22 = F::fma(u21, m12, F::mul(u22, m22));
+    __stcs(p.ga[0] + k, F::fma(w11, v11, F::mul(w12, v12)));
+    __stcs(p.ga[1] + k, F::fma(w21, v11, F::mul(w22, v12)));
+    __stcs(p.ga[2] + k, F::fma(w11, v21, F::mul(w12, v22)));
+    __stcs(p.ga[3] + k, F::fma(w21, v21, F::mul(w22, v22)));
   }
 }
 
@@ -109,17 +110,19 @@ struct BwdArgsC {
   int64_t n;
 };
 
-// sum_a conj(x_a) y_a over the two elements (a0, a1) of x and (b0, b1) of y:
-// real part (xr yr + xi yi) + (..), imaginary part (xr yi - xi yr) + (..).
+// sum_a conj(x_a) y_a over the two elements (a0, a1) of x and (b0, b1) of y,
+// each four-term sum as the fma chain x0 y0 + (x1 y1 + (x2 y2 + x3 y3)):
+// real part xr0 yr0 + xi0 yi0 + xr1 yr1 + xi1 yi1, imaginary part
+// xr0 yi0 - xi0 yr0 + xr1 yi1 - xi1 yr1.
 template <typename T>
 __device__ __forceinline__ T cdot_re(T xr0, T xi0, T yr0, T yi0, T xr1, T xi1, T yr1, T yi1) {
   using F = fp<T>;
-  return F::add(F::add(F::mul(xr0, yr0), F::mul(xi0, yi0)), F::add(F::mul(xr1, yr1), F::mul(xi1, yi1)));
+  return F::fma(xr0, yr0, F::fma(xi0, yi0, F::fma(xr1, yr1, F::mul(xi1, yi1))));
 }
 template <typename T>
 __device__ __forceinline__ T cdot_im(T xr0, T xi0, T yr0, T yi0, T xr1, T xi1, T yr1, T yi1) {
   using F = fp<T>;
-  return F::add(F::sub(F::mul(xr0, yi0), F::mul(xi0, yr0)), F::sub(F::mul(xr1, yi1), F::mul(xi1, yr1)));
+  return F::fma(xr0, yi0, F::fma(b_neg(xi0), yr0, F::fma(xr1, yi1, b_neg(F::mul(xi1, yr1)))));
 }
 
 template <typename T>
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(256) bwd_cplx_kernel(const BwdArgsC<T> p) {
     if (s1 > T(0)) {
       const T g = F::div(F::sub(s1, s2), s1);
       // g = 0: the safeguard's value there (0), also for rel_delta = 0 (0/0)
-      inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::add(F::mul(g, g), F::mul(p.dl, p.dl))));
+      inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::fma(g, g, F::mul(p.dl, p.dl))));
     }
     const T pr = F::mul(F::mul(T(0.5), F::sub(ar, br)), inv_sum);
     const T pi = F::mul(F::mul(T(0.5), F::sub(ai, bi)), inv_sum);
@@ -179,10 +182,10 @@ __global__ void __launch_bounds__(256) bwd_cplx_kernel(const BwdArgsC<T> p) {
 #pragma unroll
       for (int y = 0; y < 2; ++y) {
         const int o = x + 2 * y, u1 = x, u2 = x + 2, m1 = 2 * y, m2 = 2 * y + 1;
-        wr[o] = F::add(F::sub(F::mul(ur[u1], mr[m1]), F::mul(ui[u1], mi[m1])),
-                       F::sub(F::mul(ur[u2], mr[m2]), F::mul(ui[u2], mi[m2])));
-        wi[o] = F::add(F::add(F::mul(ur[u1], mi[m1]), F::mul(ui[u1], mr[m1])),
-                       F::add(F::mul(ur[u2], mi[m2]), F::mul(ui[u2], mr[m2])));
+        wr[o] = F::fma(ur[u1], mr[m1], F::fma(b_neg(ui[u1]), mi[m1],
+                       F::fma(ur[u2], mr[m2], b_neg(F::mul(ui[u2], mi[m2])))));
+        wi[o] = F::fma(ur[u1], mi[m1], F::fma(ui[u1], mr[m1],
+                       F::fma(ur[u2], mi[m2], F::mul(ui[u2], mr[m2]))));
       }
     }
     // gA = W V^*
@@ -191,10 +194,10 @@ __global__ void __launch_bounds__(256) bwd_cplx_kernel(const BwdArgsC<T> p) {
 #pragma unroll
       for (int y = 0; y < 2; ++y) {
         const int o = x + 2 * y, w1 = x, w2 = x + 2, v1 = y, v2 = y + 2;
-        __stcs(p.ga[2 * o] + k, F::add(F::add(F::mul(wr[w1], vr[v1]), F::mul(wi[w1], vi[v1])),
-                                       F::add(F::mul(wr[w2], vr[v2]), F::mul(wi[w2], vi[v2]))));
-        __stcs(p.ga[2 * o + 1] + k, F::add(F::sub(F::mul(wi[w1], vr[v1]), F::mul(wr[w1], vi[v1])),
-                                           F::sub(F::mul(wi[w2], vr[v2]), F::mul(wr[w2], vi[v2]))));
+        __stcs(p.ga[2 * o] + k, F::fma(wr[w1], vr[v1], F::fma(wi[w1], vi[v1],
+                                       F::fma(wr[w2], vr[v2], F::mul(wi[w2], vi[v2])))));
+        __stcs(p.ga[2 * o + 1] + k, F::fma(wi[w1], vr[v1], F::fma(b_neg(wr[w1]), vi[v1],
+                                           F::fma(wi[w2], vr[v2], b_neg(F::mul(wr[w2], vi[v2]))))));
       }
     }
   }
