@@ -627,6 +627,57 @@ def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
     return out
 
 
+def bench_host_link(torch, stream, nbytes=1 << 30, reps=5):
+    """The host link as the e2e measurement sees it: copy-engine rates of one
+    GiB between pinned host memory and the device in each direction and in
+    both at once (two streams), timed with CUDA events, and the NUMA nodes
+    (with their CPUs) this process can run on."""
+    import glob
+    nodes = {}
+    for d in sorted(glob.glob("/sys/devices/system/node/node[0-9]*")):
+        try:
+            nodes[os.path.basename(d)] = open(os.path.join(d, "cpulist")).read().strip()
+        except OSError:
+            pass
+    h = torch.empty(nbytes // 4, dtype=torch.float32).pin_memory()
+    h2 = torch.empty(nbytes // 4, dtype=torch.float32).pin_memory()
+    d = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    d2 = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    h.fill_(1.0)
+    other = torch.cuda.Stream()
+
+    def rate(f):
+        f()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    def both():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        other.wait_event(ev)
+        with torch.cuda.stream(other):
+            h2.copy_(d2, non_blocking=True)
+        d.copy_(h, non_blocking=True)
+        done = torch.cuda.Event()
+        done.record(other)
+        stream.wait_event(done)
+
+    out = {"numa_nodes": nodes, "process_cpus": len(os.sched_getaffinity(0)),
+           "h2d_GBps": rate(lambda: d.copy_(h, non_blocking=True)),
+           "d2h_GBps": rate(lambda: h.copy_(d, non_blocking=True)),
+           "both_directions_GBps": 2 * rate(both)}
+    del h, h2, d, d2
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_complex128(torch, S, stream, steps=10, warmup=3):
     """The complex128 workload (n = 2^24, parts U[-1,1] 2^e, e in [-500, 500]
     per matrix, 1% rank-deficient) on the plain FP64 form: matrices/s, the
@@ -873,6 +924,7 @@ def run_ours(args):
                 summary["fp32_tan64_smax_err_max_u"], summary["fp32_tan64_smin_err_max_u"],
                 summary["fp32_rerun_matrices_per_s"] / 1e9, summary["fp32_rerun_smin_err_max_u"]))
         report = {"precision": prec,
+                  "host_link": bench_host_link(torch, stream),
                   "complex128": bench_complex128(torch, S, stream),
                   "multi_batch": bench_multi(torch, S, stream),
                   "differentiation": bench_grad(torch, S, stream),

@@ -232,10 +232,10 @@ SFP_FN double div_fast(double a, double b, unsigned &bad) {
 // quotient are q32's (or 2^24 when q32 rounded up into the next binade), and
 // two more integer digits of 20 and 9 bits with exact residuals complete the
 // 53, on 32-bit integers (the residuals are small, so arithmetic modulo 2^32
-// gives them exactly).  Domain: a = +-0 or normal, b normal, q32 normal (a
-// quotient of floats is always a normal double); outside it bad is set and
-// the result is unspecified.
-SFP_FN double div_ff(float a, float b, float q32, unsigned &bad) {
+// gives them exactly).  div_ff_core assumes its domain: a = +-0 or normal, b
+// normal, q32 normal (a quotient of floats is always a normal double);
+// div_ff checks it, sets bad outside it (the result is then unspecified).
+SFP_FN double div_ff_core(float a, float b, float q32) {
   const uint32_t ua = fbits(a), ub = fbits(b), uq = fbits(q32);
   const uint32_t sgn = (ua ^ ub) & 0x80000000u;
   const uint32_t ea = (ua >> 23) & 0xffu, eb = (ub >> 23) & 0xffu, eq = (uq >> 23) & 0xffu;
@@ -247,21 +247,18 @@ SFP_FN double div_ff(float a, float b, float q32, unsigned &bad) {
   // is 2^(e+1)
   const bool up = (int)eq == e + 128;
   const uint32_t q0 = up ? 0x1000000u : ((uq & 0x7fffffu) | 0x800000u);
-  const bool a_zero = (ua & 0x7fffffffu) == 0;
-  bad |= (a_zero || (ea - 1u < 254u && eq - 1u < 254u && (up || (int)eq == e + 127))) &&
-                 eb - 1u < 254u ? 0u : 1u;
   // E0 = A 2^23 - q0 mb, |E0| <= mb / 2 < 2^23 (q0 is the nearest integer)
   const int32_t E0 = (int32_t)((A << 23) - q0 * mb);
   // r ~ 1/mb to ~2^-22 relative (mb < 2^24 is exact in a float)
   const float r = rcp_approx(fval(0x4B000000u | (mb & 0x7FFFFFu)));
   // digit 1 (20 bits): q1 ~ E0 2^20 / mb ~ (E0 >> 2) r 2^22, |q1| < 2^19;
-  // error <= 0.5 (truncation of E0) + 0.3 (r and roundings) + 0.5 (rounding)
+  // error <= 0.38 (truncation of E0) + 0.31 (r and roundings) + 0.5 (rounding)
   const int32_t q1 = f2i_small(fmul(fmul(i2f_small(E0 >> 2), r), 4194304.0f));
-  const int32_t E1 = (int32_t)(((uint32_t)E0 << 20) - (uint32_t)q1 * mb);   // |E1| < 1.4 mb
+  const int32_t E1 = (int32_t)(((uint32_t)E0 << 20) - (uint32_t)q1 * mb);   // |E1| < 1.2 mb
   // digit 2 (9 bits): q2 ~ E1 2^9 / mb ~ (E1 >> 5) r 2^14, |q2| < 2^10;
-  // error <= 2^-4 (truncation) + 2^-11.5 (r) + 0.5 (rounding) < 0.57
+  // error <= 2^-9 (truncation) + 2^-11 (r and roundings) + 0.5 (rounding) < 0.51
   const int32_t q2 = f2i_small(fmul(fmul(i2f_small(E1 >> 5), r), 16384.0f));
-  const int32_t E2 = (int32_t)(((uint32_t)E1 << 9) - (uint32_t)q2 * mb);    // |E2| < 0.57 mb
+  const int32_t E2 = (int32_t)(((uint32_t)E1 << 9) - (uint32_t)q2 * mb);    // |E2| < 0.51 mb
   // A 2^52 / mb = Q + E2 / mb, Q = q0 2^29 + q1 2^9 + q2: the nearest integer
   // is Q + 1 when 2 E2 > mb, Q - 1 when 2 E2 < -mb, else Q (never a tie: a
   // quotient of 24-bit integers is not half way between 53-bit ones)
@@ -271,7 +268,18 @@ SFP_FN double div_ff(float a, float b, float q32, unsigned &bad) {
   // to the exponent field of e - 1
   const uint64_t sig = ((uint64_t)q0 << 29) + (uint64_t)(int64_t)low;
   const uint64_t r64 = (((uint64_t)(e + 1023 - 1)) << 52) + sig;
+  const bool a_zero = (ua & 0x7fffffffu) == 0;
   return dval(((uint64_t)sgn << 32) | (a_zero ? 0ull : r64));
+}
+SFP_FN double div_ff(float a, float b, float q32, unsigned &bad) {
+  const uint32_t ua = fbits(a), ub = fbits(b), uq = fbits(q32);
+  const uint32_t ea = (ua >> 23) & 0xffu, eb = (ub >> 23) & 0xffu, eq = (uq >> 23) & 0xffu;
+  const uint32_t ma = (ua & 0x7fffffu) | 0x800000u, mb = (ub & 0x7fffffu) | 0x800000u;
+  const int e = (int)ea - (int)eb - (ma < mb ? 1 : 0);
+  const bool a_zero = (ua & 0x7fffffffu) == 0;
+  bad |= (a_zero || (ea - 1u < 254u && eq - 1u < 254u && ((int)eq == e + 128 || (int)eq == e + 127))) &&
+                 eb - 1u < 254u ? 0u : 1u;
+  return div_ff_core(a, b, q32);
 }
 
 // RN(a / b) for all operands: the hardware instruction outside the fast domain.
