@@ -244,6 +244,49 @@ def test_fp32_spread_boundary_of_the_fast_path():
         check(A, f"spread boundary bs={bs}", backscale=bs)
 
 
+def spread_cases_complex(seed, spreads):
+    """Complex FP32 matrices (8 split rows) whose nonzero parts span a given
+    number of binades, the largest part in every position; nearly rank-one
+    complex matrices u v^T + a few-ulp perturbation whose imaginary parts are
+    2^-k times the real ones (k up to 60: the cancellation of Eq. 7 and the
+    phase of r'_12 then leave tiny parts in r'_12, r''_22 and r'_22); and
+    real-valued ones (zero imaginary parts)."""
+    rng = np.random.default_rng(seed)
+    cols = []
+    for d in spreads:
+        for pos in range(8):
+            for _ in range(12):
+                sig = rng.uniform(1.0, 2.0, 8) * rng.choice([-1.0, 1.0], 8)
+                e = -rng.integers(0, d + 1, 8)
+                e[pos] = -d
+                e[rng.integers(0, 8)] = 0
+                cols.append(np.ldexp(sig, e))
+    for k in list(range(0, 61, 4)) + [62, 63, 64, 65]:
+        for _ in range(48):
+            u = rng.standard_normal(2) + 1j * np.ldexp(rng.standard_normal(2), -k)
+            v = rng.standard_normal(2) + 1j * np.ldexp(rng.standard_normal(2), -k)
+            M = np.outer(u, v)
+            M = M * (1 + 2.0**-23 * rng.integers(-3, 4, (2, 2)))
+            if rng.random() < 0.25:
+                M = M.real + 0j
+            # record order: a11, a21, a12, a22, each (Re, Im)
+            z = [M[0, 0], M[1, 0], M[0, 1], M[1, 1]]
+            cols.append(np.array([x for w in z for x in (w.real, w.imag)]))
+    A = np.array(cols, dtype=np.float64).T
+    return np.ascontiguousarray(A.astype(np.float32))
+
+
+def test_complex_fp32_spread_boundary_of_the_fast_path():
+    """The complex FP32 kernels run the method at the scale h - 64 when every
+    nonzero part is within 64 binades of the largest, and flag for the fix-up
+    pass any matrix whose Eq. 7 cancellation (or the phase of r'_12) leaves a
+    part of r'_12, r''_22, r'_22 below 2^-100 at that scale: spreads around the
+    boundary and such cancellations must all match the oracle bit for bit."""
+    A = spread_cases_complex(92, list(range(58, 71)) + [100, 150, 200, 240])
+    for bs in (False, True):
+        check(A, f"complex spread boundary bs={bs}", backscale=bs)
+
+
 def _sampled_check(A, what, nsample=1 << 15, seed=0):
     g = S.svd2(torch.from_numpy(A).cuda())
     torch.cuda.synchronize()
