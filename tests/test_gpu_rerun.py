@@ -112,3 +112,59 @@ def test_rerun_fixup_pass_scattered_edges(rows):
         assert_same(g, o, f"rerun fixup rows={rows} bs={bs}")
         assert cnt == o["count"]
         assert not np.isin(g["s"], [np.iinfo(np.int32).min, np.iinfo(np.int32).min + 1]).any()
+
+
+def _shape_sweep_input(rows, n):
+    if rows == 4:
+        return inputs.real_fp32_illcond(n, seed=71)[0]
+    return inputs.complex_fp32_illcond(n, seed=72)[0]
+
+
+@pytest.mark.parametrize("rows", [4, 8])
+def test_rerun_every_matrix_marked(rows):
+    """tau = 2^0: every matrix with sigma'_min < sigma'_max is re-run (the
+    index list holds the whole batch); bits and count as the oracle's, in the
+    default launch shape of the batch pass and two others."""
+    n = 2**15 + 17
+    A = inputs.normal_batch(n, rows, 73 + rows, np.float32)
+    o = oracle.svd2_rerun(A, 0)
+    assert o["count"] > n - 16
+    kind = "s" if rows == 4 else "c"
+    old = S.get_launch(kind)
+    try:
+        for shape in (old, (64, 4, 2, 0), (512, 1, 1, 4)):
+            S.set_launch(kind, *shape)
+            g, cnt = run(A, 0)
+            assert_same(g, o, f"{kind} all marked {shape}")
+            assert cnt == o["count"]
+    finally:
+        S.set_launch(kind, *old)
+
+
+@pytest.mark.parametrize("rows", [4, 8])
+def test_rerun_misaligned_rows_and_guard_bands(rows):
+    """Rows that start 4 bytes off a 16-byte boundary take one matrix per
+    thread; canaries around every output array stay untouched by all four
+    kernels (the batch pass, the compaction, the scattered re-run stores and
+    the fix-up pass)."""
+    n, pad = 30011, 64
+    A = _shape_sweep_input(rows, n + 1)
+    Ad = torch.from_numpy(A).cuda()[:, 1:]
+    o = oracle.svd2_rerun(np.ascontiguousarray(A[:, 1:]), -8)
+    canary = float.fromhex("0x1.dead0p+7")
+    bufs = [torch.full((rows, n + 1 + pad), canary, dtype=torch.float32, device="cuda")
+            for _ in range(2)]
+    sb = [torch.full((n + 1 + pad,), canary, dtype=torch.float32, device="cuda") for _ in range(2)]
+    si = torch.full((n + 1 + pad,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    out = S.Svd2Result(U=bufs[0][:, 1:n + 1], V=bufs[1][:, 1:n + 1], smax=sb[0][1:n + 1],
+                       smin=sb[1][1:n + 1], s=si[1:n + 1])
+    r = S.svd2_rerun(Ad, tau_log2=-8, out=out)
+    torch.cuda.synchronize()
+    g = {k: getattr(r, k).cpu().numpy() for k in ("U", "V", "smax", "smin", "s")}
+    assert_same(g, o, f"rows={rows} misaligned")
+    assert S.rerun_count(r.workspace) == o["count"]
+    for b in bufs:
+        assert torch.all(b[:, 0] == canary) and torch.all(b[:, n + 1:] == canary)
+    for b in sb:
+        assert b[0] == canary and torch.all(b[n + 1:] == canary)
+    assert si[0] == 0x5A5A5A5A and torch.all(si[n + 1:] == 0x5A5A5A5A)
