@@ -43,48 +43,113 @@ __device__ __forceinline__ T ld0(const T *p, int64_t k) {
   return p ? __ldcs(p + k) : T(0);
 }
 
+// M consecutive elements from k0 (vector loads), or zeros for a NULL array.
+template <typename T, int M>
+__device__ __forceinline__ void ld0_vec(const T *p, int64_t k0, T (&x)[M]) {
+  if (p) {
+    load_vec<T, M>(p + k0, x);
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) x[m] = T(0);
+  }
+}
+
+// The adjoint of one matrix: U, V, s1, s2 and the upstream gradients in,
+// gA out (element order 11, 21, 12, 22).
 template <typename T>
-__global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs<T> p) {
+__device__ __forceinline__ void bwd_one(const T (&u)[4], const T (&v)[4], T s1, T s2,
+                                        const T (&gu)[4], const T (&gv)[4], T m11, T m22, T dl,
+                                        T (&ga)[4]) {
   using F = fp<T>;
+  const T u11 = u[0], u21 = u[1], u12 = u[2], u22 = u[3];
+  const T v11 = v[0], v21 = v[1], v12 = v[2], v22 = v[3];
+  // J12 = (U^T gU)_12, J21 = (U^T gU)_21, likewise K for V
+  // (every two-term dot product as fma(x0, y0, x1 y1))
+  const T J12 = F::fma(u11, gu[2], F::mul(u21, gu[3]));
+  const T J21 = F::fma(u12, gu[0], F::mul(u22, gu[1]));
+  const T K12 = F::fma(v11, gv[2], F::mul(v21, gv[3]));
+  const T K21 = F::fma(v12, gv[0], F::mul(v22, gv[1]));
+  const T a = F::sub(J12, J21), b = F::sub(K12, K21);
+  const T sum = F::add(s1, s2);
+  const T inv_sum = sum > T(0) ? F::div(T(1), sum) : T(0);
+  T inv_gap = T(0);
+  if (s1 > T(0)) {
+    const T g = F::div(F::sub(s1, s2), s1);
+    // g = 0: the safeguard's value there (0), also for rel_delta = 0 (0/0)
+    inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::fma(g, g, F::mul(dl, dl))));
+  }
+  const T pp = F::mul(F::mul(T(0.5), F::sub(a, b)), inv_sum);
+  const T qq = F::mul(F::mul(T(0.5), F::add(a, b)), inv_gap);
+  const T m12 = F::sub(pp, qq), m21 = F::sub(b_neg(pp), qq);
+  // W = U M, gA = W V^T
+  const T w11 = F::fma(u11, m11, F::mul(u12, m21));
+  const T w12 = F::fma(u11, m12, F::mul(u12, m22));
+  const T w21 = F::fma(u21, m11, F::mul(u22, m21));
+  const T w22 = F::fma(u21, m12, F::mul(u22, m22));
+  ga[0] = F::fma(w11, v11, F::mul(w12, v12));
+  ga[1] = F::fma(w21, v11, F::mul(w22, v12));
+  ga[2] = F::fma(w11, v21, F::mul(w12, v22));
+  ga[3] = F::fma(w21, v21, F::mul(w22, v22));
+}
+
+// M matrices per thread per step (grid-stride), every array read and written
+// with M-element vector accesses (all arrays aligned to M elements; M = 1:
+// scalar accesses at any alignment), then the n mod M tail one per thread.
+template <typename T, int M>
+__global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs<T> p) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride) {
-    const T u11 = __ldcs(p.u[0] + k), u21 = __ldcs(p.u[1] + k);
-    const T u12 = __ldcs(p.u[2] + k), u22 = __ldcs(p.u[3] + k);
-    const T v11 = __ldcs(p.v[0] + k), v21 = __ldcs(p.v[1] + k);
-    const T v12 = __ldcs(p.v[2] + k), v22 = __ldcs(p.v[3] + k);
-    const T s1 = __ldcs(p.s1 + k), s2 = __ldcs(p.s2 + k);
-    const T gu11 = ld0(p.gu[0], k), gu21 = ld0(p.gu[1], k);
-    const T gu12 = ld0(p.gu[2], k), gu22 = ld0(p.gu[3], k);
-    const T gv11 = ld0(p.gv[0], k), gv21 = ld0(p.gv[1], k);
-    const T gv12 = ld0(p.gv[2], k), gv22 = ld0(p.gv[3], k);
-    // J12 = (U^T gU)_12, J21 = (U^T gU)_21, likewise K for V
-    // (every two-term dot product as fma(x0, y0, x1 y1))
-    const T J12 = F::fma(u11, gu12, F::mul(u21, gu22));
-    const T J21 = F::fma(u12, gu11, F::mul(u22, gu21));
-    const T K12 = F::fma(v11, gv12, F::mul(v21, gv22));
-    const T K21 = F::fma(v12, gv11, F::mul(v22, gv21));
-    const T a = F::sub(J12, J21), b = F::sub(K12, K21);
-    const T sum = F::add(s1, s2);
-    const T inv_sum = sum > T(0) ? F::div(T(1), sum) : T(0);
-    T inv_gap = T(0);
-    if (s1 > T(0)) {
-      const T g = F::div(F::sub(s1, s2), s1);
-      // g = 0: the safeguard's value there (0), also for rel_delta = 0 (0/0)
-      inv_gap = g == T(0) ? T(0) : F::div(g, F::mul(s1, F::fma(g, g, F::mul(p.dl, p.dl))));
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ngroups = p.n / M;
+  for (int64_t g = tid; g < ngroups; g += stride) {
+    const int64_t k0 = g * M;
+    T u[4][M], v[4][M], gu[4][M], gv[4][M], s1[M], s2[M], m11[M], m22[M], ga[4][M];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      load_vec<T, M>(p.u[e] + k0, u[e]);
+      load_vec<T, M>(p.v[e] + k0, v[e]);
     }
-    const T pp = F::mul(F::mul(T(0.5), F::sub(a, b)), inv_sum);
-    const T qq = F::mul(F::mul(T(0.5), F::add(a, b)), inv_gap);
-    const T m11 = ld0(p.g1, k), m22 = ld0(p.g2, k);
-    const T m12 = F::sub(pp, qq), m21 = F::sub(b_neg(pp), qq);
-    // W = U M, gA = W V^T
-    const T w11 = F::fma(u11, m11, F::mul(u12, m21));
-    const T w12 = F::fma(u11, m12, F::mul(u12, m22));
-    const T w21 = F::fma(u21, m11, F::mul(u22, m21));
-    const T w22 = F::fma(u21, m12, F::mul(u22, m22));
-    __stcs(p.ga[0] + k, F::fma(w11, v11, F::mul(w12, v12)));
-    __stcs(p.ga[1] + k, F::fma(w21, v11, F::mul(w22, v12)));
-    __stcs(p.ga[2] + k, F::fma(w11, v21, F::mul(w12, v22)));
-    __stcs(p.ga[3] + k, F::fma(w21, v21, F::mul(w22, v22)));
+    load_vec<T, M>(p.s1 + k0, s1);
+    load_vec<T, M>(p.s2 + k0, s2);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ld0_vec<T, M>(p.gu[e], k0, gu[e]);
+      ld0_vec<T, M>(p.gv[e], k0, gv[e]);
+    }
+    ld0_vec<T, M>(p.g1, k0, m11);
+    ld0_vec<T, M>(p.g2, k0, m22);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      T ui[4], vi[4], gui[4], gvi[4], gai[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ui[e] = u[e][m];
+        vi[e] = v[e][m];
+        gui[e] = gu[e][m];
+        gvi[e] = gv[e][m];
+      }
+      bwd_one<T>(ui, vi, s1[m], s2[m], gui, gvi, m11[m], m22[m], p.dl, gai);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) ga[e][m] = gai[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) store_vec<T, M>(p.ga[e] + k0, ga[e]);
+  }
+  if constexpr (M > 1) {
+    const int64_t k = ngroups * M + tid;
+    if (k < p.n) {
+      T ui[4], vi[4], gui[4], gvi[4], gai[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ui[e] = __ldcs(p.u[e] + k);
+        vi[e] = __ldcs(p.v[e] + k);
+        gui[e] = ld0(p.gu[e], k);
+        gvi[e] = ld0(p.gv[e], k);
+      }
+      bwd_one<T>(ui, vi, __ldcs(p.s1 + k), __ldcs(p.s2 + k), gui, gvi, ld0(p.g1, k),
+                 ld0(p.g2, k), p.dl, gai);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) __stcs(p.ga[e] + k, gai[e]);
+    }
   }
 }
 
@@ -254,10 +319,28 @@ static int launch_bwd(int64_t n, const T *const *U, const T *const *V, const T *
   p.g2 = g2;
   p.dl = rel_delta;
   p.n = n;
-  const int64_t want = (n + 255) / 256;
+  // FP32: two matrices per thread (8-byte vector accesses) when every array
+  // allows it -- the FP32 adjoint is bound by memory latency; the FP64 one, bound
+  // by the FP64 pipe, keeps one matrix per thread (61 registers; 102 with two)
+  const size_t va = 2 * sizeof(T);
+  bool vec = sizeof(T) == 4 && aligned(s1, va) && aligned(s2, va) && (!g1 || aligned(g1, va)) &&
+             (!g2 || aligned(g2, va));
+  for (int e = 0; e < 4; ++e)
+    vec = vec && aligned(U[e], va) && aligned(V[e], va) && aligned(gA[e], va) &&
+          (!p.gu[e] || aligned(p.gu[e], va)) && (!p.gv[e] || aligned(p.gv[e], va));
+  const int M = vec ? 2 : 1;
+  const int64_t units = (n / M > n % M) ? n / M : n % M;   // threads needed
+  const int64_t want = (units + 255) / 256;
   const int64_t cap = (int64_t)sm_count() * 8;
-  const unsigned grid = (unsigned)(want < cap ? want : cap);
-  bwd_kernel<T><<<grid, 256, 0, stream>>>(p);
+  const unsigned grid = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+  if constexpr (sizeof(T) == 4) {
+    if (vec)
+      bwd_kernel<T, 2><<<grid, 256, 0, stream>>>(p);
+    else
+      bwd_kernel<T, 1><<<grid, 256, 0, stream>>>(p);
+  } else {
+    bwd_kernel<T, 1><<<grid, 256, 0, stream>>>(p);
+  }
   SVD2_CUDA_TRY(cudaGetLastError());
   return SVD2_OK;
 }

@@ -90,6 +90,35 @@ def test_bwd_null_gradients_are_zero():
     assert bits_equal(gA.cpu().numpy(), o)
 
 
+def test_bwd_fp32_vector_and_scalar_paths():
+    """The FP32 adjoint takes two matrices per thread when every array is
+    8-byte aligned and one otherwise (arrays 4 bytes off): both give the
+    oracle's bits, with and without NULL upstream gradients, on an odd n (the
+    tail of the two-per-thread path)."""
+    A, gU, gV, gS = _edge_and_batch(2**16 + 1, np.float32)
+    n = A.shape[1]
+    r = S.svd2(_dev(A, torch.float32), backscale=True)
+    dl = S.default_rel_delta(torch.float32)
+    Uh, Vh = r.U.cpu().numpy(), r.V.cpu().numpy()
+    s1h, s2h = r.smax.cpu().numpy(), r.smin.cpu().numpy()
+
+    def off(x):   # a copy whose data start 4 bytes past an 8-byte boundary
+        x = np.ascontiguousarray(x)
+        buf = torch.zeros(x.shape[:-1] + (x.shape[-1] + 1,), dtype=torch.float32, device="cuda")
+        buf[..., 1:] = torch.from_numpy(x).cuda()
+        return buf[..., 1:]
+
+    z4, z1 = np.zeros_like(gU), np.zeros_like(gS[0])
+    for with_grads in (True, False):
+        o = oracle.bwd(Uh, Vh, s1h, s2h, gU if with_grads else z4, gV, gS[0],
+                       gS[1] if with_grads else z1, dl)
+        for mk in (lambda x: _dev(x, torch.float32), off):
+            gA = S.svd2_bwd(mk(Uh), mk(Vh), mk(s1h), mk(s2h), mk(gU) if with_grads else None,
+                            mk(gV), mk(gS[0]), mk(gS[1]) if with_grads else None, dl)
+            torch.cuda.synchronize()
+            assert bits_equal(gA.cpu().numpy(), o), (with_grads, n)
+
+
 def _natural(ref, gU, gV, s1, s2):
     return np.maximum(np.abs(ref).max(axis=0),
                       (np.abs(gU).max(axis=0) + np.abs(gV).max(axis=0)) / (s1 - s2))
