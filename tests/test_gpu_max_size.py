@@ -1,9 +1,9 @@
 """Batches past 2^31 matrices: every index of the split layout is 64-bit in
 the kernels, the grid-stride loops run past the 32-bit range, and the re-run
-form splits such a batch into launches.  A real FP32 batch of n = 2^31 + 7
-matrices (N(0,1) entries drawn on the GPU, 120 GB of inputs and outputs, plus
-8 GB of re-run workspace) with ill-conditioned and edge matrices planted at
-the start, across index 2^31 and at the end; sampled outputs of the plain FP32
+form splits such a batch into launches.  A real FP32 batch of just over 2^31
+matrices (n = 2^31 + 2^16 + 7; N(0,1) entries drawn on the GPU; 120 GB of
+inputs and outputs, plus 8 GB of re-run workspace) with ill-conditioned and
+edge matrices planted at the start, across index 2^31 and at the end; sampled outputs of the plain FP32
 form, the FP64 tangent-step form and the FP64 re-run form against the oracle,
 bit for bit.  Skipped on a device with less free memory than it needs."""
 import numpy as np
@@ -17,7 +17,7 @@ from tests.test_gpu_fwd import assert_same
 
 pytestmark = pytest.mark.gpu
 
-N = 2**31 + 7
+N = 2**31 + 2**16 + 7
 NEED = 140 * 2**30
 
 
@@ -61,13 +61,13 @@ def test_forms_past_2_31_matrices():
     with np.errstate(all="ignore"):
         S.svd2(A, out=out)
         torch.cuda.synchronize()
-        assert_same(_take(out, it), oracle.svd2(Asub), "plain FP32, n = 2^31 + 7")
+        assert_same(_take(out, it), oracle.svd2(Asub), "plain FP32, n = 2^31 + 2^16 + 7")
         S.svd2_tan64(A, tau_log2=S.TAN64_TAU_LOG2, out=out)
         torch.cuda.synchronize()
         assert_same(_take(out, it), oracle.svd2_tan64(Asub, S.TAN64_TAU_LOG2),
-                    "FP64 tangent step, n = 2^31 + 7")
+                    "FP64 tangent step, n = 2^31 + 2^16 + 7")
         r = S.svd2_rerun(A, tau_log2=S.RERUN_TAU_LOG2, out=out)
         torch.cuda.synchronize()
         o = oracle.svd2_rerun(Asub, S.RERUN_TAU_LOG2)
-        assert_same(_take(out, it), o, "FP64 re-run, n = 2^31 + 7")
+        assert_same(_take(out, it), o, "FP64 re-run, n = 2^31 + 2^16 + 7")
         assert S.rerun_count(r.workspace) >= o["count"] > 0
