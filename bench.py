@@ -120,6 +120,14 @@ def parse():
                    help="skip the FP32-vs-FP64 comparison and the supplementary report")
     p.add_argument("--report", default="",
                    help="write the supplementary report (JSON) to this file instead of stderr")
+    p.add_argument("--multi-batches", type=int, default=0,
+                   help="profiling mode: time only the multi-batch launch on the first K "
+                        "batches of the 2048-batch sequence and print one JSON line")
+    p.add_argument("--multi-grid", type=int, default=0,
+                   help="with --multi-batches: 0 = one block per tile, G > 0 = a grid of G "
+                        "blocks walking the tiles (persistent when G is at most the resident count)")
+    p.add_argument("--multi-shape", default="256,1,1",
+                   help="with --multi-batches: block,mpt,unroll of the launch")
     return p.parse_args()
 
 
@@ -945,12 +953,40 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def run_multi_profile(args):
+    """The multi-batch launch alone on the first K batches of the 2048-batch
+    sequence (the Kogbetliantz batching workload), in one launch shape and
+    grid, timed with CUDA events over --steps launches after --warmup; for
+    comparing one block per tile with a persistent grid under a profiler."""
+    import torch
+    from paper_2005_07403_gb300 import inputs
+    from paper_2005_07403_gb300 import svd2 as S
+    lens, cplx = inputs.kog_batches()
+    k = min(args.multi_batches, len(lens))
+    lens, cplx = lens[:k], cplx[:k]
+    dev = [inputs.normal_batch_device(int(n), 8 if c else 4, 5000 + i)
+           for i, (n, c) in enumerate(zip(lens, cplx))]
+    block, mpt, unroll = (int(x) for x in args.multi_shape.split(","))
+    mb = S.MultiBatch(dev, block=block, mpt=mpt, unroll=unroll)
+    stream = torch.cuda.current_stream()
+    ms = time_steps(torch, lambda: mb.run(grid=args.multi_grid), args.steps, args.warmup, stream)
+    total = int(lens.sum())
+    nbytes = int(sum(n * (212 if c else 116) for n, c in zip(lens, cplx)))
+    print(json.dumps({"multi_batches": k, "matrices": total, "complex_fraction": float(cplx.mean()),
+                      "shape": [block, mpt, unroll], "grid": args.multi_grid, "tiles": mb.tiles,
+                      "ms": ms, "matrices_per_s": total / (ms / 1e3),
+                      "algorithmic_GBps": nbytes / (ms / 1e3) / 1e9}), flush=True)
+
+
 def main():
     if "--sources-digest" in sys.argv:
         for w in KERNEL_SOURCES:
             print(w, sources_digest(w))
         return
     args = parse()
+    if args.multi_batches > 0:
+        run_multi_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
