@@ -37,14 +37,18 @@ def test_reference_arm_prints_one_complete_line(workload):
         <= 1e-6 * d["ms_per_step"]
 
 
-def test_recorded_traffic_needs_the_current_digest_and_scales_with_n(monkeypatch):
+def test_recorded_traffic_needs_the_recorded_digest_and_scales_with_n(monkeypatch):
     w = "real-fp32-tan64"
-    t1 = bench.recorded_traffic(w, 2**24)
-    assert t1 is not None and t1 > 0
-    assert bench.recorded_traffic(w, 2**26) == pytest.approx(4 * t1, rel=1e-12)
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+        row = next(ln.split() for ln in f if ln.split()[:1] == [w])
+    digest, n_cap, rd, wr = row[1], int(row[3]), float(row[4]), float(row[5])
+    # sources with the recorded digest: the capture scaled to n
+    monkeypatch.setattr(bench, "sources_digest", lambda workload: digest)
+    assert bench.recorded_traffic(w, n_cap) == pytest.approx(rd + wr, rel=1e-12)
+    assert bench.recorded_traffic(w, 4 * n_cap) == pytest.approx(4 * (rd + wr), rel=1e-12)
     # the traffic of a kernel whose sources changed is not reported
     monkeypatch.setattr(bench, "sources_digest", lambda workload: "0000000000000000")
-    assert bench.recorded_traffic(w, 2**24) is None
+    assert bench.recorded_traffic(w, n_cap) is None
 
 
 class _Done:
