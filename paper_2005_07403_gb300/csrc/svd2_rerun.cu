@@ -19,6 +19,8 @@
 // re-run by the FP64 and integer pipes.  The re-run's gathers and scattered
 // 4-byte stores touch about 0.7 sectors per array and re-run matrix (one in
 // ten matrices at the 2^-8 threshold on the ill-conditioned mix).
+#include <type_traits>
+
 #include "svd2_fwd_impl.cuh"
 
 namespace svd2 {
@@ -68,11 +70,16 @@ __device__ __forceinline__ int32_t rerun_one(Ar &ar, const FwdArgs<float, CPLX ?
   return s32;
 }
 
-// Arithmetic of the double-precision re-run: the general arithmetic, whose
-// division and square root run on the integer pipe, so that the FP64 pipe (2
-// results per clock per SM) executes only the method's own operations;
-// measured faster than the hardware division and square root here.
-using RerunAr = ExactAr<double>;
+// Arithmetic of the double-precision re-run; its division and square root run
+// on the integer pipe either way, so that the FP64 pipe (2 results per clock
+// per SM) executes only the method's own operations.  Complex: the batch
+// kernels' branch-free fast arithmetic (a matrix outside its domain gets
+// s = kRedoRerun and the fix-up pass re-runs it with the general arithmetic);
+// real: the general arithmetic.  Measured on the list of the 2^24 batch: real
+// 198 us general against 221 us fast, complex (2^23) 254 us general against
+// 239 us fast.
+template <bool CPLX>
+using RerunAr = typename std::conditional<CPLX, FastAr<double>, ExactAr<double>>::type;
 
 // Pass 2: the indices k with s[k] == kRerunMark, in increasing order within
 // each chunk of 16 * blockDim.x matrices (one warp-scan and one block-scan of
@@ -141,7 +148,7 @@ __global__ void __launch_bounds__(512, 2)
     float a[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) a[e] = p.a[e][k];
-    RerunAr ar;
+    RerunAr<CPLX> ar;
     const int32_t s32 = rerun_one<CPLX>(ar, p, k, a);
     if (ar.bad) {                       // the fix-up kernel re-runs it exactly
       p.s[k] = kRedoRerun;
