@@ -30,6 +30,7 @@ struct Stage {
   size_t bytes = 0;                      // per slot
   cudaStream_t st[3] = {nullptr, nullptr, nullptr};   // h2d, compute, d2h
   cudaEvent_t in_ready[2] = {}, computed[2] = {}, out_done[2] = {};
+  cudaEvent_t start = nullptr;           // the caller's stream at the call
   bool init = false;
 };
 
@@ -44,6 +45,7 @@ int setup(Stage &S, size_t slot_bytes) {
       SVD2_CUDA_TRY(cudaEventCreateWithFlags(&S.computed[b], cudaEventDisableTiming));
       SVD2_CUDA_TRY(cudaEventCreateWithFlags(&S.out_done[b], cudaEventDisableTiming));
     }
+    SVD2_CUDA_TRY(cudaEventCreateWithFlags(&S.start, cudaEventDisableTiming));
     S.init = true;
   }
   if (S.bytes < slot_bytes) {
@@ -132,12 +134,10 @@ extern "C" int svd2_batch_host(int op, int64_t n, const void *const *A, void *co
   int rc = setup(S, slot);
   if (rc != SVD2_OK) return rc;
   const cudaStream_t caller = (cudaStream_t)stream;
-  // the pipeline starts after the caller's prior work
-  cudaEvent_t start = nullptr;
-  SVD2_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-  SVD2_CUDA_TRY(cudaEventRecord(start, caller));
-  SVD2_CUDA_TRY(cudaStreamWaitEvent(S.st[0], start, 0));
-  cudaEventDestroy(start);
+  // the pipeline starts after the caller's prior work (calls are serialised
+  // by g_mu, so one event per device serves every call)
+  SVD2_CUDA_TRY(cudaEventRecord(S.start, caller));
+  SVD2_CUDA_TRY(cudaStreamWaitEvent(S.st[0], S.start, 0));
   // ... and after the previous call's chunks have left both slots
   for (int b = 0; b < 2; ++b) SVD2_CUDA_TRY(cudaStreamWaitEvent(S.st[0], S.out_done[b], 0));
   const int64_t nchunks = (n + c - 1) / c;
