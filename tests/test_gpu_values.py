@@ -111,3 +111,33 @@ def test_interleaved_reconstructs_torch_matrices():
     R = U @ Sg @ V.conj().transpose(1, 2)
     err = (R - M).abs().amax(dim=(1, 2)) / M.abs().amax(dim=(1, 2))
     assert float(err.max()) < 8 * 2.0**-52
+
+
+@pytest.mark.parametrize("rows,dtype", [(4, np.float32), (4, np.float64), (8, np.float32)])
+def test_interleaved_unaligned_records_take_the_element_path(rows, dtype):
+    """Records whose base is off a 16-byte boundary (one real element, or one
+    complex64 element, past it): the kernel reads and writes the interleaved
+    layout element by element at its stride (no record vectors); outputs as
+    the oracle's."""
+    n = 2**15 + 3
+    A = _batch(rows, dtype, n, 131 + rows)
+    M = np.ascontiguousarray(_to_interleaved(A))
+    tdt = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+    off = 2 if rows == 8 else 1                       # scalars before the first record
+    flat = torch.zeros(M.size * (2 if rows == 8 else 1) + off, dtype=tdt, device="cuda")
+    src = torch.from_numpy(M).cuda()
+    flat[off:] = (torch.view_as_real(src) if rows == 8 else src).reshape(-1)
+    if rows == 8:
+        Mu = torch.view_as_complex(flat[off:].view(n, 2, 2, 2))
+    else:
+        Mu = flat[off:].view(n, 2, 2)
+    assert Mu.data_ptr() % 16 != 0
+    r = S.svd2_interleaved(Mu)
+    torch.cuda.synchronize()
+    with np.errstate(all="ignore"):
+        o = oracle.svd2(A)
+    assert bits_equal(_to_split(r.U.cpu().numpy()), o["U"])
+    assert bits_equal(_to_split(r.V.cpu().numpy()), o["V"])
+    assert bits_equal(r.smax.cpu().numpy(), o["smax"])
+    assert bits_equal(r.smin.cpu().numpy(), o["smin"])
+    assert np.array_equal(r.s.cpu().numpy(), o["s"])
