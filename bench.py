@@ -920,6 +920,13 @@ def run_ours(args):
         summary, prec = compare_precisions(torch, S, max(3, min(args.steps, 10)), args.warmup,
                                            stream)
         line["fp32_vs_fp64"] = summary
+        # the comparison also as scalars in config, which records of the line
+        # keep where they reduce nested keys to their names
+        for k in ("fp64_matrices_per_s", "fp64_fp64_pipe_frac", "fp32_plain_matrices_per_s",
+                  "fp32_plain_smin_err_max_u", "fp32_tan64_smax_err_max_u",
+                  "fp32_tan64_smin_err_max_u", "fp32_tan64_double_fraction",
+                  "fp32_rerun_matrices_per_s", "fp32_rerun_smin_err_max_u"):
+            line["config"]["vs_" + k] = summary[k]
         line["config"]["compare"] = (
             "same n=2^26 inputs: FP64 %.1f G/s (%.2f of FP64 pipe); FP32 %.1f G/s (%.2f of HBM), "
             "sigma'_min err vs FP64 up to %.3g u; FP32 + FP64 tangent step %.1f G/s (%.2f of HBM), "
