@@ -116,6 +116,9 @@ def parse():
                    help="override the batch size (small cases for profiling only)")
     p.add_argument("--no-tune", action="store_true",
                    help="keep the library's default launch shape")
+    p.add_argument("--launch", default="",
+                   help="block,mpt,unroll,waves: this launch shape for the workload's kernel "
+                        "(no tuning; for profiling a given shape)")
     p.add_argument("--no-compare", action="store_true",
                    help="skip the FP32-vs-FP64 comparison and the supplementary report")
     p.add_argument("--report", default="",
@@ -810,7 +813,10 @@ def run_ours(args):
     call = _caller(S, W, Ad, out, workspace, G)
     S.lib()
     tuned = None
-    if not args.no_tune:
+    kind_launch = {"tan64": "s_tan64"}.get(W["form"], W["kind"])
+    if args.launch:
+        S.set_launch(kind_launch, *(int(x) for x in args.launch.split(",")))
+    elif not args.no_tune:
         from paper_2005_07403_gb300 import tune
         # launch shape from the autotuner (cached)
         tuned = tune.tune(Ad, out, reps=3, form="tan64" if W["form"] == "tan64" else "plain")
@@ -905,9 +911,9 @@ def run_ours(args):
             "dtype": W["dtype"], "data": "synthetic",
             "config": {"workload": W["desc"], "n_per_gpu": n,
                        "l2": "inputs larger than L2 (>= 1 GiB per step)",
-                       "launch": "block %d, mpt %d, unroll %d, waves %d" % S.get_launch(
-                           "s_tan64" if W["form"] == "tan64" else W["kind"]),
-                       "launch_from": "autotuner" if tuned else "default"},
+                       "launch": "block %d, mpt %d, unroll %d, waves %d" % S.get_launch(kind_launch),
+                       "launch_from": ("given" if args.launch else
+                                       "autotuner" if tuned else "default")},
             "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk}
     if W["form"] == "tan64":

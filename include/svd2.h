@@ -371,7 +371,7 @@ int svd2_graph_destroy(void *graph_exec);
  * 2 = s, 3 = c, 4 = svd2_batch_s_tan64 at SVD2_TAN64_TAU_LOG2) on the caller's
  * batch (arguments as for svd2_batch_*) for every block in {64, 128, 256,
  * 512, 1024} that the op admits (see svd2_set_launch), mpt in {1, 2, 4},
- * unroll in {1, 2} and waves in {0, 4}, `reps` timed launches each after one
+ * unroll in {1, 2} and waves in {0, 1, 2, 4}, `reps` timed launches each after one
  * warm-up launch, sets the fastest as the op's launch shape and returns it
  * with its time per launch (ms).  svd2_multi_autotune does the same for the
  * multi-batch launch (block in {64, 128, 256, 512, 1024}, mpt in {1, 2, 4},

@@ -35,7 +35,7 @@ static Launch g_launch[kNumOps] = {
     {512, 1, 1, 0},   // z
     {512, 2, 1, 4},   // s
     {256, 2, 1, 0},   // c
-    {1024, 2, 1, 4},  // s with the FP64 tangent step
+    {1024, 4, 1, 2},  // s with the FP64 tangent step
 };
 
 Launch get_launch(int op) {
