@@ -342,6 +342,44 @@ SFP_FN double sqrt_fast(double x, unsigned &bad) {
   return sqrt_core(ux);
 }
 
+// RN(a b) on the integer pipe, for a and b normal or zero and a product that is
+// zero or normal; otherwise the result is unspecified and bad is set.  The
+// 53-bit significands ma, mb are split at bit 32 (ma = ah 2^32 + al, ah < 2^21),
+// the 106-bit product P = ma mb is formed from four 32 x 32 -> 64-bit products
+// (P in [2^104, 2^106)), normalized to [2^105, 2^106) by one left shift when
+// below, and rounded to nearest even at bit 53: the significand is P >> 53, the
+// round bit bit 52, the sticky bits 0 - 51.  A carry of the rounding into 2^53
+// moves into the exponent field.  (The FP64 pipe of GB300 executes 2
+// operations per clock per SM; this trades one of them for integer
+// instructions.)
+SFP_FN double mul_fast(double a, double b, unsigned &bad) {
+  const uint64_t ua = dbits(a), ub = dbits(b);
+  const uint32_t ha = (uint32_t)(ua >> 32), hb = (uint32_t)(ub >> 32);
+  const uint32_t la = (uint32_t)ua, lb = (uint32_t)ub;
+  const uint32_t ea = (ha >> 20) & 0x7ffu, eb = (hb >> 20) & 0x7ffu;
+  const uint32_t sgn = (ha ^ hb) & 0x80000000u;
+  const bool zero = ((ua << 1) == 0) || ((ub << 1) == 0);
+  const uint32_t mah = (ha & 0xfffffu) | 0x100000u, mbh = (hb & 0xfffffu) | 0x100000u;
+  const uint64_t ll = (uint64_t)la * lb;
+  const uint64_t mid = (uint64_t)la * mbh + (uint64_t)mah * lb;        // < 2^54
+  const uint64_t lo = ll + (mid << 32);
+  const uint64_t hi = (uint64_t)mah * mbh + (mid >> 32) + (lo < ll ? 1u : 0u);   // P >> 64, < 2^42
+  // normalize: P < 2^105 (bit 41 of hi clear) moves up by one
+  const uint32_t top = (uint32_t)(hi >> 41) & 1u;
+  const uint64_t h2 = top ? hi : (hi << 1) | (lo >> 63);
+  const uint64_t l2 = top ? lo : lo << 1;
+  const uint64_t sig = (h2 << 11) | (l2 >> 53);                       // in [2^52, 2^53)
+  const uint64_t rbit = (l2 >> 52) & 1u;
+  const uint64_t sticky = (l2 << 12) != 0 ? 1u : 0u;
+  const uint64_t inc = rbit & (sticky | (sig & 1u));
+  const int e = (int)ea + (int)eb - 1023 + (int)top;                   // biased exponent
+  const uint64_t r = ((uint64_t)(uint32_t)(e - 1) << 52) + sig + inc;
+  const bool in_ok = (ea - 1u < 2046u || (ua << 1) == 0) && (eb - 1u < 2046u || (ub << 1) == 0);
+  const bool out_ok = zero || (e >= 1 && (uint32_t)(r >> 52) - 1u < 2046u);
+  bad |= (in_ok && out_ok) ? 0u : 1u;
+  return dval(((uint64_t)sgn << 32) | (zero ? 0ull : r));
+}
+
 // RN(sqrt(x)) for all x: the hardware instruction outside the fast domain.
 SFP_FN double sqrt_rn(double x) {
   const uint64_t ux = dbits(x);

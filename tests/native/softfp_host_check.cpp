@@ -87,6 +87,26 @@ static void chk_f2d(uint32_t b) {
   }
 }
 
+// the integer-pipe multiplication: where it does not flag the operands, the
+// CPU's product; it flags no pair of normal operands whose product is normal
+// and above the smallest normal (a product rounded up to the smallest normal
+// from below it is flagged: its exponent is below the range before rounding)
+static long long mul_flagged = 0;
+static void chk_mul(double a, double b) {
+  unsigned flag = 0;
+  const double r = svd2::sfp::mul_fast(a, b, flag), h = a * b;
+  ++checked;
+  const bool normal_in = (std::fpclassify(a) == FP_NORMAL || a == 0) &&
+                         (std::fpclassify(b) == FP_NORMAL || b == 0);
+  const bool normal_out = (std::fpclassify(h) == FP_NORMAL && std::fabs(h) > 0x1p-1022) ||
+                          (h == 0 && (a == 0 || b == 0));
+  if (flag) ++mul_flagged;
+  if ((!flag && dbits(r) != dbits(h)) || (flag && normal_in && normal_out)) {
+    if (bad < 10) std::printf("mul_fast mismatch a=%a b=%a soft=%a hw=%a flag=%u\n", a, b, r, h, flag);
+    ++bad;
+  }
+}
+
 // the float-quotient division: where it does not flag the operands, the CPU's
 // double quotient of the widened floats, given the CPU's float quotient
 static long long ff_checked = 0;
@@ -140,7 +160,30 @@ int main(int argc, char **argv) {
       for (uint32_t fa : {0u, 1u, 0x7fffffu, 0x400000u, fb, fb ^ 1u, fb + 1u})
         for (uint32_t ea : {1u, 100u, 127u, 128u, 254u}) chk_div_ff(fmk(0, ea, fa), fmk(0, eb, fb));
     }
+  // products: zeros of both signs, exact powers of two, the ends of the
+  // exponent range (results at the normal boundary and the overflow threshold)
+  for (int sa = 0; sa < 2; ++sa)
+    for (int sb = 0; sb < 2; ++sb)
+      for (uint64_t e : {1ull, 1023ull, 2046ull}) {
+        chk_mul(mk(sa, 0, 0), mk(sb, e, 0x123456789abcull));
+        chk_mul(mk(sa, e, 0xfffffffffffffull), mk(sb, 0, 0));
+        chk_mul(mk(sa, e, 0), mk(sb, 1023, 0));
+        for (uint64_t f : {0ull, 1ull, 0xfffffffffffffull, 0x8000000000000ull})
+          for (uint64_t e2 : {1ull, 2ull, 1022ull, 1023ull, 1024ull, 2045ull, 2046ull})
+            chk_mul(mk(sa, e, f), mk(sb, e2, 0xfffffffffffffull ^ f));
+      }
   for (long long i = 0; i < n; ++i) {
+    {
+      // products: random significands with exponents around 1, anywhere in the
+      // range (under- and overflowing results flagged), structured mantissas,
+      // and halfway cases (a significand times 1 + 2^-k)
+      const uint64_t e1 = 1023 + (sm64(s) % 64) - 32, e2 = 1023 + (sm64(s) % 64) - 32;
+      chk_mul(mk(sm64(s) & 1, e1, sm64(s)), mk(sm64(s) & 1, e2, sm64(s)));
+      chk_mul(mk(sm64(s) & 1, 1 + sm64(s) % 2046, sm64(s)), mk(sm64(s) & 1, 1 + sm64(s) % 2046, sm64(s)));
+      chk_mul(mk(0, e1, specials[sm64(s) % 14]), mk(1, e2, specials[sm64(s) % 14]));
+      chk_mul(mk(0, e1, sm64(s) << 20), mk(0, e2, (1ull << (sm64(s) % 52))));
+      chk_mul(dval(sm64(s)), dval(sm64(s)));
+    }
     {
       // float quotients: random significands, exponents near each other and
       // anywhere, numerators below the divisor (the method's use), small
