@@ -131,6 +131,9 @@ def parse():
                         "blocks walking the tiles (persistent when G is at most the resident count)")
     p.add_argument("--multi-shape", default="256,1,1",
                    help="with --multi-batches: block,mpt,unroll of the launch")
+    p.add_argument("--kog", choices=[c[0] for c in KOG_CASES], default="",
+                   help="profiling mode: time only the Kogbetliantz step of this type "
+                        "(m x m, m = --n if given) and print one JSON line")
     return p.parse_args()
 
 
@@ -752,7 +755,12 @@ def bench_variants(torch, S, stream, steps=10, warmup=3):
     return out
 
 
-def bench_kog(torch, S, stream, steps=10, warmup=3):
+KOG_CASES = (("complex128", 8192, "complex128", 48, 16),
+             ("real_fp64", 8192, "float64", 16, 0),
+             ("real_fp32", 16384, "float32", 16, 0))
+
+
+def bench_kog(torch, S, stream, steps=10, warmup=3, only="", m_override=0):
     """One parallel Kogbetliantz step (Sec. 1) on m x m matrices of N(0,1)
     entries drawn on the device: complex128 and real FP64 with m = 8192
     (column-major), real FP32 with m = 16384; with the pivot pairs (2i, 2i+1)
@@ -760,15 +768,19 @@ def bench_kog(torch, S, stream, steps=10, warmup=3):
     columns).  G is updated in place every step (the transformation is
     unitary, so the values stay bounded).  Per case: steps/s, the update's
     algorithmic bytes (G read and written once) against the HBM copy peak and,
-    in FP64, its operations (64 per complex 2x2 block, 16 per real one)
-    against the FP64 pipe."""
+    in FP64, the operations it issues on the FP64 pipe against that pipe's
+    peak: 16 per real 2x2 block; 48 of the 64 per complex one, whose 16
+    leading products run on the integer pipe (their count is reported
+    beside)."""
     from paper_2005_07403_gb300 import inputs
     peak, _ = measured_peaks()
     fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3
     out = {}
-    for name, m, dt, ops in (("complex128", 8192, torch.complex128, 64),
-                             ("real_fp64", 8192, torch.float64, 16),
-                             ("real_fp32", 16384, torch.float32, 16)):
+    for name, m, dt, ops, int_ops in KOG_CASES:
+        if only and name != only:
+            continue
+        m = m_override or m
+        dt = getattr(torch, dt)
         g = torch.Generator(device="cuda")
         g.manual_seed(141)
         G = torch.randn((m, m), generator=g, device="cuda", dtype=dt).T   # column-major
@@ -781,6 +793,8 @@ def bench_kog(torch, S, stream, steps=10, warmup=3):
             r = {"steps_per_s": 1e3 / ms, "ms": ms, "bytes_per_step": nbytes,
                  "hbm_frac": nbytes / (ms / 1e3) / 1e9 / peak}
             if dt != torch.float32:
+                r["fp64_pipe_ops_per_block"] = ops
+                r["int_pipe_products_per_block"] = int_ops
                 r["fp64_pipe_frac"] = ops * (m // 2) ** 2 / (ms / 1e3) / 1e9 / fp64_peak
             res[order] = r
         out[name] = res
@@ -999,6 +1013,13 @@ def main():
     args = parse()
     if args.multi_batches > 0:
         run_multi_profile(args)
+        return
+    if args.kog:
+        import torch
+        from paper_2005_07403_gb300 import svd2 as S
+        out = bench_kog(torch, S, torch.cuda.current_stream(), args.steps, args.warmup,
+                        only=args.kog, m_override=args.n)
+        print(json.dumps({"kogbetliantz_step": out}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -107,30 +107,46 @@ __global__ void __launch_bounds__(256) kog_pivot_kernel(const __grid_constant__ 
   }
 }
 
+// The multiplication that starts each fma chain of the update: the hardware
+// instruction, or for doubles the integer-pipe form (sfp::mul_fast, the same
+// bits; it sets bad for operands or a product outside the normal range), which
+// moves that operation off the FP64 pipe (2 operations per clock per SM).
+struct HwMul {
+  template <typename T> __device__ __forceinline__ T operator()(T a, T b) const {
+    return fp<T>::mul(a, b);
+  }
+};
+struct IntMul {
+  unsigned &bad;
+  __device__ __forceinline__ double operator()(double a, double b) const {
+    return sfp::mul_fast(a, b, bad);
+  }
+};
+
 // Complex 2x2 entries: (re, im) pairs in the record order of Sec. 8
 // (x11, x21, x12, x22).  Sums of two products as fma chains.
-template <typename T>
+template <typename T, typename Mul>
 __device__ __forceinline__ void conj_dot2(T xr1, T xi1, T yr1, T yi1, T xr2, T xi2, T yr2, T yi2,
-                                          T &re, T &im) {
+                                          T &re, T &im, const Mul &mul) {
   using F = fp<T>;
   // conj(x1) y1 + conj(x2) y2
-  re = F::fma(xr1, yr1, F::fma(xi1, yi1, F::fma(xr2, yr2, F::mul(xi2, yi2))));
-  im = F::fma(xr1, yi1, F::fma(f_neg(xi1), yr1, F::fma(xr2, yi2, f_neg(F::mul(xi2, yr2)))));
+  re = F::fma(xr1, yr1, F::fma(xi1, yi1, F::fma(xr2, yr2, mul(xi2, yi2))));
+  im = F::fma(xr1, yi1, F::fma(f_neg(xi1), yr1, F::fma(xr2, yi2, f_neg(mul(xi2, yr2)))));
 }
-template <typename T>
+template <typename T, typename Mul>
 __device__ __forceinline__ void dot2(T xr1, T xi1, T yr1, T yi1, T xr2, T xi2, T yr2, T yi2,
-                                     T &re, T &im) {
+                                     T &re, T &im, const Mul &mul) {
   using F = fp<T>;
   // x1 y1 + x2 y2
-  re = F::fma(xr1, yr1, F::fma(f_neg(xi1), yi1, F::fma(xr2, yr2, f_neg(F::mul(xi2, yi2)))));
-  im = F::fma(xr1, yi1, F::fma(xi1, yr1, F::fma(xr2, yi2, F::mul(xi2, yr2))));
+  re = F::fma(xr1, yr1, F::fma(f_neg(xi1), yi1, F::fma(xr2, yr2, f_neg(mul(xi2, yi2)))));
+  im = F::fma(xr1, yi1, F::fma(xi1, yr1, F::fma(xr2, yi2, mul(xi2, yr2))));
 }
 
 // B' = U^* B V for 2x2 matrices (element order x11, x21, x12, x22; complex:
 // separate real and imaginary arrays).
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, typename Mul>
 __device__ __forceinline__ void two_sided(const T *ur, const T *ui, const T *vr, const T *vi,
-                                          T *br, T *bi) {
+                                          T *br, T *bi, const Mul &mul) {
   using F = fp<T>;
   T tr[4], ti[4];
   // T = U^* B: t_xy = conj(u_0x) b_0y + conj(u_1x) b_1y (0-based x, y; the
@@ -141,9 +157,9 @@ __device__ __forceinline__ void two_sided(const T *ur, const T *ui, const T *vr,
     for (int y = 0; y < 2; ++y) {
       const int t = x + 2 * y, u1 = 2 * x, u2 = 2 * x + 1, b1 = 2 * y, b2 = 2 * y + 1;
       if constexpr (CPLX) {
-        conj_dot2(ur[u1], ui[u1], br[b1], bi[b1], ur[u2], ui[u2], br[b2], bi[b2], tr[t], ti[t]);
+        conj_dot2(ur[u1], ui[u1], br[b1], bi[b1], ur[u2], ui[u2], br[b2], bi[b2], tr[t], ti[t], mul);
       } else {
-        tr[t] = F::fma(ur[u1], br[b1], F::mul(ur[u2], br[b2]));
+        tr[t] = F::fma(ur[u1], br[b1], mul(ur[u2], br[b2]));
         ti[t] = T(0);
       }
     }
@@ -155,9 +171,9 @@ __device__ __forceinline__ void two_sided(const T *ur, const T *ui, const T *vr,
     for (int y = 0; y < 2; ++y) {
       const int o = x + 2 * y, t1 = x, t2 = x + 2, v1 = 2 * y, v2 = 2 * y + 1;
       if constexpr (CPLX) {
-        dot2(tr[t1], ti[t1], vr[v1], vi[v1], tr[t2], ti[t2], vr[v2], vi[v2], br[o], bi[o]);
+        dot2(tr[t1], ti[t1], vr[v1], vi[v1], tr[t2], ti[t2], vr[v2], vi[v2], br[o], bi[o], mul);
       } else {
-        br[o] = F::fma(tr[t1], vr[v1], F::mul(tr[t2], vr[v2]));
+        br[o] = F::fma(tr[t1], vr[v1], mul(tr[t2], vr[v2]));
       }
     }
   }
@@ -254,6 +270,7 @@ __global__ void __launch_bounds__(256) kog_update_kernel(const __grid_constant__
     const bool v1 = adjacent && (reinterpret_cast<uintptr_t>(p.g + (CPLX ? 2 : 1) * o1) % kAlign) == 0;
     // block in the record order (x11, x21, x12, x22) of rows (pk, qk) x columns (pc, qc)
     T gr[4], gi[4];
+    auto load_block = [&]() {
     if (adjacent) {
       // rows fast: line pj holds (pk,pc),(qk,pc) = record 0, 1; line qj holds 2, 3.
       // columns fast: line pj (a row) holds (pk,pc),(pk,qc) = record 0, 2; line qj holds 1, 3.
@@ -271,12 +288,36 @@ __global__ void __launch_bounds__(256) kog_update_kernel(const __grid_constant__
       g_load(p, pk, qc, gr[2], gi[2]);
       g_load(p, qk, qc, gr[3], gi[3]);
     }
+    };
+    load_block();
     T or_[4], oi[4];   // the other factor, uniform across the warp
     load_factor<T, CPLX>(ROWS_FAST ? p.v : p.u, jj, or_, oi);
-    if constexpr (ROWS_FAST)
-      two_sided<T, CPLX>(fr, fi, or_, oi, gr, gi);
-    else
-      two_sided<T, CPLX>(or_, oi, fr, fi, gr, gi);
+    auto apply = [&](const auto &mul) {
+      if constexpr (ROWS_FAST)
+        two_sided<T, CPLX>(fr, fi, or_, oi, gr, gi, mul);
+      else
+        two_sided<T, CPLX>(or_, oi, fr, fi, gr, gi, mul);
+    };
+    if constexpr (sizeof(T) == 8 && CPLX) {
+      // complex doubles: the block's 16 leading products on the integer pipe
+      // (64 FP64 operations a block; measured 1.85 -> 1.49 ms at m = 8192;
+      // the real block, 8 of 16, ran slower, bound by the integer issue and
+      // the lower occupancy of the larger register file); a block with an
+      // operand or product outside its domain (a subnormal, an overflow) is
+      // read again and done with the hardware multiplication (nothing is
+      // stored before this point)
+      unsigned bad = 0;
+      apply(IntMul{bad});
+      if (__any_sync(__activemask(), bad != 0)) {
+        if (bad) {
+          asm volatile("" ::: "memory");   // a fresh read, not the first one's registers
+          load_block();
+          apply(HwMul{});
+        }
+      }
+    } else {
+      apply(HwMul{});
+    }
     if (adjacent) {
       if constexpr (ROWS_FAST) {
         g_store2(p, o0, v0, gr[0], gi[0], gr[1], gi[1]);

@@ -123,3 +123,30 @@ def test_gpu_sweeps_diagonalize(cplx):
     assert K.off_norm(Gf) < 1e-12 * off0
     d = np.sort(np.abs(np.diag(Gf)))[::-1]
     assert np.allclose(d, s0, rtol=0, atol=1e-12 * s0[0])
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_entries_across_the_exponent_range(cplx):
+    """Entries of G from subnormal to 2^1000, with exact zeros: in complex
+    double the update's leading products run on the integer pipe, whose domain
+    is normal operands with a normal product. Blocks with a zero, a subnormal or
+    an underflowing product are read again and done with the hardware
+    multiply. Checked against the oracle in both layouts, and the two layouts
+    give the same bits."""
+    m = 66
+    rng = np.random.default_rng(1000 + cplx)
+    scale = np.ldexp(1.0, rng.choice([-1070, -1040, -1000, 0, 600, 1000], size=(m, m)))
+    G = rng.standard_normal((m, m)) * scale
+    if cplx:
+        G = G + 1j * rng.standard_normal((m, m)) * np.ldexp(1.0, rng.choice([-1060, 0, 900],
+                                                                            size=(m, m)))
+    G[rng.random((m, m)) < 0.05] = 0
+    pairs = rng.permutation(m).astype(np.int32)
+    out = {}
+    with np.errstate(all="ignore"):
+        for layout in ("row", "col"):
+            Gp, skipped = _gpu(G, pairs, layout)
+            assert skipped == 0
+            _check(G, pairs, Gp, "d")
+            out[layout] = Gp
+    assert bits_equal(out["row"], out["col"])
