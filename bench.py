@@ -176,12 +176,14 @@ FP64_OPS_PER_MATRIX = {"z": 89, "d": 34}
 FP64_OPS_VALUES_Z = 89 - 38
 
 
-# The translation unit each workload's kernels are built from; every digest
+# The translation units each workload's kernels are built from (the
+# differentiation step: the forward kernel's and the adjoint's); every digest
 # also covers the shared headers, the C header and the build script.
 KERNEL_SOURCES = {"complex128": "svd2_fwd_z.cu", "real-fp64": "svd2_fwd_d.cu",
                   "real-fp32": "svd2_fwd_s.cu", "real-fp32-rerun": "svd2_rerun.cu",
-                  "real-fp32-tan64": "svd2_tan64.cu", "grad-fp64": "svd2_bwd.cu",
-                  "grad-fp32": "svd2_bwd.cu",
+                  "real-fp32-tan64": "svd2_tan64.cu",
+                  "grad-fp64": ("svd2_fwd_d.cu", "svd2_bwd.cu"),
+                  "grad-fp32": ("svd2_fwd_s.cu", "svd2_bwd.cu"),
                   "complex64": "svd2_fwd_c.cu", "complex64-rerun": "svd2_rerun.cu"}
 
 
@@ -192,8 +194,10 @@ def sources_digest(workload):
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join("paper_2005_07403_gb300", "csrc")
-    files = [os.path.join("include", "svd2.h"), os.path.join("paper_2005_07403_gb300", "build.py"),
-             os.path.join(csrc, KERNEL_SOURCES[workload])]
+    tus = KERNEL_SOURCES[workload]
+    tus = (tus,) if isinstance(tus, str) else tus
+    files = [os.path.join("include", "svd2.h"), os.path.join("paper_2005_07403_gb300", "build.py")]
+    files += [os.path.join(csrc, tu) for tu in tus]
     files += sorted(os.path.join(csrc, f) for f in os.listdir(os.path.join(ROOT, csrc))
                     if f.endswith(".cuh"))
     import re
@@ -756,7 +760,7 @@ def bench_variants(torch, S, stream, steps=10, warmup=3):
 
 
 KOG_CASES = (("complex128", 8192, "complex128", 48, 16),
-             ("real_fp64", 8192, "float64", 16, 0),
+             ("real_fp64", 8192, "float64", 12, 4),
              ("real_fp32", 16384, "float32", 16, 0))
 
 
@@ -769,9 +773,9 @@ def bench_kog(torch, S, stream, steps=10, warmup=3, only="", m_override=0):
     unitary, so the values stay bounded).  Per case: steps/s, the update's
     algorithmic bytes (G read and written once) against the HBM copy peak and,
     in FP64, the operations it issues on the FP64 pipe against that pipe's
-    peak: 16 per real 2x2 block; 48 of the 64 per complex one, whose 16
-    leading products run on the integer pipe (their count is reported
-    beside)."""
+    peak: 12 of the 16 per real 2x2 block and 48 of the 64 per complex one,
+    the rest leading products of the fma chains run on the integer pipe
+    (their count is reported beside)."""
     from paper_2005_07403_gb300 import inputs
     peak, _ = measured_peaks()
     fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3

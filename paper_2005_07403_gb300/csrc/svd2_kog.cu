@@ -144,9 +144,9 @@ __device__ __forceinline__ void dot2(T xr1, T xi1, T yr1, T yi1, T xr2, T xi2, T
 
 // B' = U^* B V for 2x2 matrices (element order x11, x21, x12, x22; complex:
 // separate real and imaginary arrays).
-template <typename T, bool CPLX, typename Mul>
+template <typename T, bool CPLX, typename Mul, typename Mul2 = Mul>
 __device__ __forceinline__ void two_sided(const T *ur, const T *ui, const T *vr, const T *vi,
-                                          T *br, T *bi, const Mul &mul) {
+                                          T *br, T *bi, const Mul &mul, const Mul2 &mul2) {
   using F = fp<T>;
   T tr[4], ti[4];
   // T = U^* B: t_xy = conj(u_0x) b_0y + conj(u_1x) b_1y (0-based x, y; the
@@ -171,9 +171,9 @@ __device__ __forceinline__ void two_sided(const T *ur, const T *ui, const T *vr,
     for (int y = 0; y < 2; ++y) {
       const int o = x + 2 * y, t1 = x, t2 = x + 2, v1 = 2 * y, v2 = 2 * y + 1;
       if constexpr (CPLX) {
-        dot2(tr[t1], ti[t1], vr[v1], vi[v1], tr[t2], ti[t2], vr[v2], vi[v2], br[o], bi[o], mul);
+        dot2(tr[t1], ti[t1], vr[v1], vi[v1], tr[t2], ti[t2], vr[v2], vi[v2], br[o], bi[o], mul2);
       } else {
-        br[o] = F::fma(tr[t1], vr[v1], mul(tr[t2], vr[v2]));
+        br[o] = F::fma(tr[t1], vr[v1], mul2(tr[t2], vr[v2]));
       }
     }
   }
@@ -236,8 +236,20 @@ __device__ __forceinline__ void g_store2(const KogArgs<T, CPLX> &p, int64_t o, b
   }
 }
 
+// Launch shape of the update kernel, by measurement at m = 8192 (column-major,
+// pairs (2i, 2i+1)): complex doubles in blocks of 128 with at least 5 resident
+// per SM (96 registers; 1.38 ms against 1.49 at 2 blocks of 256 and 122
+// registers, 1.41 at 3 blocks and 80); real doubles 4 blocks of 256 (64
+// registers; 0.38 ms against 0.39 at 3 blocks and 76); floats as the compiler
+// allots.
+template <typename T, bool CPLX> struct KogShape {
+  static constexpr int block = (CPLX && sizeof(T) == 8) ? 128 : 256;
+  static constexpr int min_blocks = sizeof(T) != 8 ? 0 : CPLX ? 5 : 4;
+};
+
 template <typename T, bool CPLX, bool ROWS_FAST>
-__global__ void __launch_bounds__(256) kog_update_kernel(const __grid_constant__ KogArgs<T, CPLX> p) {
+__global__ void __launch_bounds__(KogShape<T, CPLX>::block, KogShape<T, CPLX>::min_blocks)
+    kog_update_kernel(const __grid_constant__ KogArgs<T, CPLX> p) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.npairs) return;
   const int32_t pi = p.pairs[2 * i], qi = p.pairs[2 * i + 1];
@@ -292,31 +304,34 @@ __global__ void __launch_bounds__(256) kog_update_kernel(const __grid_constant__
     load_block();
     T or_[4], oi[4];   // the other factor, uniform across the warp
     load_factor<T, CPLX>(ROWS_FAST ? p.v : p.u, jj, or_, oi);
-    auto apply = [&](const auto &mul) {
+    auto apply = [&](const auto &mul, const auto &mul2) {
       if constexpr (ROWS_FAST)
-        two_sided<T, CPLX>(fr, fi, or_, oi, gr, gi, mul);
+        two_sided<T, CPLX>(fr, fi, or_, oi, gr, gi, mul, mul2);
       else
-        two_sided<T, CPLX>(or_, oi, fr, fi, gr, gi, mul);
+        two_sided<T, CPLX>(or_, oi, fr, fi, gr, gi, mul, mul2);
     };
-    if constexpr (sizeof(T) == 8 && CPLX) {
-      // complex doubles: the block's 16 leading products on the integer pipe
-      // (64 FP64 operations a block; measured 1.85 -> 1.49 ms at m = 8192;
-      // the real block, 8 of 16, ran slower, bound by the integer issue and
-      // the lower occupancy of the larger register file); a block with an
-      // operand or product outside its domain (a subnormal, an overflow) is
+    if constexpr (sizeof(T) == 8) {
+      // doubles: leading products of the fma chains on the integer pipe --
+      // all 16 of a complex block (64 FP64 operations; 1.85 -> 1.49 ms at
+      // m = 8192 in the same launch shape), the 4 of the first stage of a
+      // real one (16 operations; 0.49 -> 0.38 ms); a block with an operand or
+      // product outside the multiply's domain (zero, subnormal, overflow) is
       // read again and done with the hardware multiplication (nothing is
       // stored before this point)
       unsigned bad = 0;
-      apply(IntMul{bad});
+      if constexpr (CPLX)
+        apply(IntMul{bad}, IntMul{bad});
+      else   // the 4 products of U^* B (all 8: 0.49 ms against 0.38)
+        apply(IntMul{bad}, HwMul{});
       if (__any_sync(__activemask(), bad != 0)) {
         if (bad) {
           asm volatile("" ::: "memory");   // a fresh read, not the first one's registers
           load_block();
-          apply(HwMul{});
+          apply(HwMul{}, HwMul{});
         }
       }
     } else {
-      apply(HwMul{});
+      apply(HwMul{}, HwMul{});
     }
     if (adjacent) {
       if constexpr (ROWS_FAST) {
@@ -377,11 +392,12 @@ int kog_step(int64_t m, T *G, int64_t rs, int64_t cs, const int32_t *pairs, void
   SVD2_CUDA_TRY(cudaGetLastError());
   // each thread takes up to 8 blocks of its line (amortises its own factor)
   const int64_t gy = (p.npairs + 7) / 8;
-  const dim3 grid((unsigned)pb, (unsigned)(gy < 65535 ? gy : 65535));
+  constexpr int ub = KogShape<T, CPLX>::block;
+  const dim3 grid((unsigned)((p.npairs + ub - 1) / ub), (unsigned)(gy < 65535 ? gy : 65535));
   if (rows_fast)
-    kog_update_kernel<T, CPLX, true><<<grid, 256, 0, st>>>(p);
+    kog_update_kernel<T, CPLX, true><<<grid, ub, 0, st>>>(p);
   else
-    kog_update_kernel<T, CPLX, false><<<grid, 256, 0, st>>>(p);
+    kog_update_kernel<T, CPLX, false><<<grid, ub, 0, st>>>(p);
   SVD2_CUDA_TRY(cudaGetLastError());
   return SVD2_OK;
 }
