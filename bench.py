@@ -596,9 +596,11 @@ def bench_multi(torch, S, stream, replays=20):
 # g1, g2 read and gA written once (real: 20 + 4 values, complex: 36 + 8), and
 # the real FP64 adjoint's FP64 add/mul/fma per matrix counted from its
 # formulas (J and K 8, a and b 2, s1 + s2 1, the gap 4, p and q 6, M 2, U M 8,
-# (U M) V^T 8; its three divisions run on the integer pipe).
+# (U M) V^T 8; its three divisions run on the integer pipe, and so do 10 of
+# its 18 products: those of p, q, the gap and (U M) V^T).
 BWD_BYTES = {"fp64": 24 * 8, "fp32": 24 * 4, "complex128": 44 * 8, "complex64": 44 * 4}
 BWD_FP64_OPS_REAL = 39
+BWD_INT_PIPE_PRODUCTS_REAL = 10
 
 
 def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
@@ -638,6 +640,7 @@ def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
                "bwd_hbm_frac": BWD_BYTES[name] * n / (msb / 1e3) / 1e9 / peak}
         if name == "fp64":
             res["bwd_fp64_ops_per_matrix"] = BWD_FP64_OPS_REAL
+            res["bwd_int_pipe_products_per_matrix"] = BWD_INT_PIPE_PRODUCTS_REAL
             res["bwd_fp64_pipe_frac"] = BWD_FP64_OPS_REAL * n / (msb / 1e3) / 1e9 / fp64_peak
         out[name] = res
         del A, gU, gV, gS, r, gA
@@ -914,12 +917,17 @@ def run_ours(args):
         ops = FP64_OPS_PER_MATRIX[W["kind"]] + (BWD_FP64_OPS_REAL if W["form"] == "grad" else 0)
         fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3   # G op/s
         fp64_achieved = ops * n / (ms_per_step / 1e3) / 1e9
+        # products of the method that the kernels run on the integer pipe
+        # (counted in ops, the method's algorithmic count, not on the FP64 pipe)
+        on_int = (8 if W["kind"] == "z" and W["form"] == "plain" else 0) + \
+            (BWD_INT_PIPE_PRODUCTS_REAL if W["form"] == "grad" else 0)
         roofline = {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak,
                     "unit": "G FP64 op/s", "frac": fp64_achieved / fp64_peak,
                     "traffic": traffic,
-                    "note": f"FP64 pipe: {ops} FP64 add/mul/fma per matrix x {n} per launch; "
-                            f"peak derived: {GB300_SMS} SMs x {GB300_FP64_PER_SM_CLK} per clock "
-                            f"x {sm_max_mhz():.0f} MHz",
+                    "note": f"FP64 pipe: {ops} FP64 add/mul/fma per matrix (the method's count; "
+                            f"{on_int} of them products run on the integer pipe) x {n} per "
+                            f"launch; peak derived: {GB300_SMS} SMs x {GB300_FP64_PER_SM_CLK} "
+                            f"per clock x {sm_max_mhz():.0f} MHz",
                     "hbm": hbm}
     else:
         roofline = hbm

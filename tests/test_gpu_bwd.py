@@ -234,3 +234,32 @@ def test_full_size_gradient_workload_sampled():
     gap = (Ss[0] - Ss[1]) / Ss[0]
     err = np.abs((grad - hi) - lo).max(axis=0) / _natural(hi, gU[:, idx], gV[:, idx], Ss[0], Ss[1])
     assert np.all(err <= 16 * EPS64 / gap), float((err * gap / EPS64).max())
+
+
+def test_bwd_fp64_across_the_exponent_range():
+    """Upstream gradients from subnormal to 2^300, with zeros, on matrices
+    scaled by 2^-300, 1 or 2^300: in FP64 the adjoint's products run on the
+    integer pipe, whose domain is normal operands with a normal product, and a
+    matrix with a product outside it is read again and done with the hardware
+    multiply.  Bit for bit against the oracle's adjoint (every value finite)."""
+    n = 4099
+    g = inputs.grad_batch(n, seed=91)
+    rng = np.random.default_rng(92)
+    A = np.ascontiguousarray(g["A"] * np.ldexp(1.0, rng.choice([-300, 0, 300], size=n)))
+
+    def grad(*shape):
+        x = rng.standard_normal(shape) * np.ldexp(1.0, rng.choice([-1070, -1040, -600, 0, 300],
+                                                                  size=shape))
+        x[rng.random(shape) < 0.05] = 0.0
+        return x
+
+    gU, gV, gS = grad(4, n), grad(4, n), grad(2, n)
+    r = S.svd2(_dev(A), backscale=True)
+    dl = S.default_rel_delta(torch.float64)
+    gA = S.svd2_bwd(r.U, r.V, r.smax, r.smin, _dev(gU), _dev(gV), _dev(gS[0]), _dev(gS[1]), dl)
+    torch.cuda.synchronize()
+    with np.errstate(all="ignore"):
+        o = oracle.bwd(r.U.cpu().numpy(), r.V.cpu().numpy(), r.smax.cpu().numpy(),
+                       r.smin.cpu().numpy(), gU, gV, gS[0], gS[1], dl)
+    assert np.isfinite(o).all()
+    assert bits_equal(gA.cpu().numpy(), o)
