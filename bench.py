@@ -131,6 +131,9 @@ def parse():
                         "blocks walking the tiles (persistent when G is at most the resident count)")
     p.add_argument("--multi-shape", default="256,1,1",
                    help="with --multi-batches: block,mpt,unroll of the launch")
+    p.add_argument("--grad", choices=["fp64", "fp32", "complex128", "complex64"], default="",
+                   help="profiling mode: time only the forward and the adjoint of this type "
+                        "(n = --n if given, else 2^22) and print one JSON line")
     p.add_argument("--kog", choices=[c[0] for c in KOG_CASES], default="",
                    help="profiling mode: time only the Kogbetliantz step of this type "
                         "(m x m, m = --n if given) and print one JSON line")
@@ -603,7 +606,7 @@ BWD_FP64_OPS_REAL = 39
 BWD_INT_PIPE_PRODUCTS_REAL = 10
 
 
-def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
+def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22, only=""):
     """The differentiation workload: A = R(t1) diag(s1, s2) R(t2)^T, 10% with
     relative gaps in [1e-12, 1e-6], N(0,1) upstream gradients (complex: N(0,1)
     parts drawn on the device).  Per dtype: the forward kernel (with
@@ -613,7 +616,7 @@ def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
     from paper_2005_07403_gb300 import inputs
     peak, _ = measured_peaks()
     fp64_peak = GB300_SMS * GB300_FP64_PER_SM_CLK * sm_max_mhz() / 1e3
-    g = inputs.grad_batch(n)
+    g = inputs.grad_batch(n) if only in ("", "fp64", "fp32") else None
     out = {"n": n}
     cases = []
     for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
@@ -627,6 +630,8 @@ def bench_grad(torch, S, stream, steps=10, warmup=3, n=2**22):
                                                inputs.normal_batch_device(n, 8, 153, "cuda", dt),
                                                inputs.normal_batch_device(n, 2, 154, "cuda", dt))))
     for name, rows, make in cases:
+        if only and name != only:
+            continue
         A, gU, gV, gS = make()
         r = S.empty_result(rows, n, A.dtype, A.device)
         gA = torch.empty_like(A)
@@ -1025,6 +1030,13 @@ def main():
     args = parse()
     if args.multi_batches > 0:
         run_multi_profile(args)
+        return
+    if args.grad:
+        import torch
+        from paper_2005_07403_gb300 import svd2 as S
+        out = bench_grad(torch, S, torch.cuda.current_stream(), args.steps, args.warmup,
+                         n=args.n or 2**22, only=args.grad)
+        print(json.dumps({"differentiation": out}), flush=True)
         return
     if args.kog:
         import torch
