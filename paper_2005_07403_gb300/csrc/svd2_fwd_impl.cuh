@@ -69,13 +69,14 @@ __device__ __forceinline__ void backscale(Ar &ar, T &smax, T &smin, int32_t &s) 
 }
 
 // One matrix with the given arithmetic policy (Sec. 2 - Sec. 7, Eq. 29; with
-// SINE, U by Eq. 31).
-template <typename T, bool CPLX, bool SINE = false, typename Ar>
+// SINE, U by Eq. 31; with VALS, the singular values and s only -- u and v are
+// then left zero in the complex method and unspecified in the real one).
+template <typename T, bool CPLX, bool SINE = false, bool VALS = false, typename Ar>
 __device__ __forceinline__ void svd2_one(Ar &ar, const T *a, T *u, T *v, T &smax, T &smin,
                                          int32_t &s) {
   int piv;
   if constexpr (CPLX)
-    svd2_cplx<T, SINE>(ar, a, u, v, smax, smin, s, piv);
+    svd2_cplx<T, SINE, VALS>(ar, a, u, v, smax, smin, s, piv);
   else
     svd2_real<T, SINE>(ar, a, u, v, smax, smin, s, piv);
 }
@@ -98,7 +99,7 @@ __device__ __forceinline__ SigmaPair<T> exact_one(const T *const *a, T *const *u
 #pragma unroll
   for (int e = 0; e < NA; ++e) ai[e] = a[e][k * stride];
   ExactAr<T> ar;
-  svd2_one<T, CPLX, SINE>(ar, ai, uo, vo, sx, sn, so);
+  svd2_one<T, CPLX, SINE, VALS>(ar, ai, uo, vo, sx, sn, so);
   const SigmaPair<T> r{sx, sn};
   if (flags & SVD2_BACKSCALE) backscale(sx, sn, so);
   if constexpr (!VALS) {
@@ -143,7 +144,7 @@ __device__ __forceinline__ unsigned process_group(const FwdArgs<T, CPLX ? 8 : 4>
     for (int e = 0; e < NA; ++e) a[e] = in[e][m];
     typename GroupArOf<T, CPLX, TAN64>::type ar;
     if constexpr (TAN64) ar.tau = p.tau;
-    svd2_one<T, CPLX, SINE>(ar, a, u, v, sx[m], sn[m], so[m]);
+    svd2_one<T, CPLX, SINE, VALS>(ar, a, u, v, sx[m], sn[m], so[m]);
     bool mark = false;
     if constexpr (MARK) mark = sn[m] < fp<T>::mul(p.tau, sx[m]);
     if (p.flags & SVD2_BACKSCALE) backscale(ar, sx[m], sn[m], so[m]);
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(256, 2 * kMinBlocks<T, CPLX>) strided_kernel(c
       for (int e = 0; e < NA; ++e) a[e] = __ldcs(p.a[e] + k * p.stride);
     }
     HotAr<T, CPLX> ar;
-    svd2_one<T, CPLX>(ar, a, u, v, sx, sn, so);
+    svd2_one<T, CPLX, false, VALS>(ar, a, u, v, sx, sn, so);
     if (p.flags & SVD2_BACKSCALE) backscale(ar, sx, sn, so);
     if constexpr (!VALS) {
       if constexpr (REC) {
